@@ -1,0 +1,78 @@
+"""Planted mistakes in the oracle must trip its pins (CPU only).
+
+Each case patches one plausible error into the oracle -- a wrong stencil
+weight, a dropped 1/h^d source scaling, a flipped Born-source sign, an
+off-by-one time index in the imaging condition -- and checks that the
+closed-form or invariant pin that guards that part of the oracle fails.
+"""
+import numpy as np
+import pytest
+
+import oracle.wave as ow
+from analytic import green2d_trace, ricker_fn
+from oracle.fd import laplacian
+from workloads import mini_config
+
+C, F0, T0 = 2000.0, 15.0, 1.5 / 15.0
+
+
+def _green_err(prob_cls=ow.Problem):
+    n, h, dt = 81, 10.0, 1e-3
+    ic, k = n // 2, 10
+    nt = 351
+    w = ricker_fn(F0, T0)(np.arange(nt) * dt)
+    p = prob_cls(np.full((n, n), 1 / C ** 2), (h, h), dt, nt, 20, [[ic, ic]], [[ic, ic + k]], w)
+    d = p.forward(0)[:, 0]
+    ua = green2d_trace(ricker_fn(F0, T0), h * k, C, np.arange(nt) * dt)
+    return np.linalg.norm(d - ua) / np.linalg.norm(ua)
+
+
+def _dot_mismatch():
+    wl = mini_config(2, shape=(20, 22), nt=160, ns=1, pad=6)
+    p = ow.problem_from_workload(wl)
+    rng = np.random.default_rng(1)
+    dm = rng.standard_normal(wl.shape)
+    r = rng.standard_normal((p.nt, p.nr))
+    a, b = np.vdot(p.born(0, dm), r), np.vdot(dm, p.adjoint(0, r))
+    return abs(a - b) / max(abs(a), abs(b))
+
+
+def test_unmutated_baseline():
+    assert _green_err() < 5e-3
+    assert _dot_mismatch() < 1e-12
+
+
+def test_wrong_stencil_weight_is_caught(monkeypatch):
+    bad = [-205 / 72, 8 / 5, +1 / 5, 8 / 315, -1 / 560]
+    monkeypatch.setattr(ow, "laplacian", lambda u, h: laplacian(u, h, weights=bad))
+    assert _green_err() > 5e-2
+
+
+def test_dropped_source_scaling_is_caught(monkeypatch):
+    def src(self, shot, n, rhs):
+        idx = tuple(int(c[shot]) for c in self.src_p)
+        rhs[idx] += self.w[n]                     # missing 1/(h_1 h_2)
+    monkeypatch.setattr(ow.Problem, "_source_rhs", src)
+    assert _green_err() > 0.5
+
+
+def test_flipped_born_sign_is_caught(monkeypatch):
+    orig = ow.Problem.born
+
+    def born(self, shot, dm, m_int=None):
+        return orig(self, shot, -np.asarray(dm), m_int)
+    monkeypatch.setattr(ow.Problem, "born", born)
+    # F flips sign while F* does not: the transposition pin breaks
+    assert _dot_mismatch() > 1.0
+
+
+def test_imaging_time_index_shift_is_caught(monkeypatch):
+    orig = ow.Problem._dtt_segments
+
+    def shifted(self, shot, m_int, ckpt):
+        prev = None
+        for n, d in orig(self, shot, m_int, ckpt):
+            yield n, (d if prev is None else prev)     # uses Dtt u^{n+1} at step n
+            prev = d
+    monkeypatch.setattr(ow.Problem, "_dtt_segments", shifted)
+    assert _dot_mismatch() > 1e-4
