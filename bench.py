@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 matrix-probing hot path: H = F*F applied over all shots.
+
+One *step* is one application of the normal operator H = F*F (Born forward
+sweep, checkpointed recompute, adjoint + imaging sweep, stacked over all shots)
+to the workload's trial function.  The default workload is the 2D 501x501
+(541x541 padded) layered model with 32 shots, nt = 2500, dt = 0.8 ms, 12 Hz
+Ricker, receivers at every surface node and dm = 200 random-sign Gaussian bumps
+(seeded synthetic inputs from ``workloads``).
+
+Printed JSON line (rank 0):
+  value        Gcell-updates/s of the batched path (all shots resident, fused
+               incident+Born forward), device-resident inputs, CUDA events on
+               the launching stream, max over ranks;
+  e2e          the same metric through the C ABI with host (NumPy) buffers,
+               host<->device copies inside the timed region;
+  roofline     the dominant kernel (fused forward step): algorithmic bytes per
+               launch / average launch duration, against the measured HBM copy
+               bandwidth;
+  plain        the plain per-shot FP32 path (one shot at a time);
+  cpu_baseline the FP64 oracle on a bounded sample of the same workload.
+``--impl reference`` times the oracle itself (rank 0 only) on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s and H-applies/s on 1 GB300, batched vs plain, % HBM peak at stated error"
+UNIT = "Gcell-updates/s"
+L2_BYTES = 129e6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--snapshot", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--profile", default=None, choices=["fwd", "adj"],
+                    help="run only F (fwd) or F* (adj) once after one warm-up call: the small "
+                         "command used for ncu captures of one kernel")
+    ap.add_argument("--shots", type=int, default=0, help="use only the first N shots (0 = all)")
+    return ap.parse_args()
+
+
+def profile_run(a, wl):
+    """One warm-up call and one measured call of F or F* (for ncu); prints a JSON line."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge._build_module().build()
+    from paper_1101_3615_gb300 import Probe
+    dev = torch.device("cuda", 0)
+    p = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet, snapshot_dtype=a.snapshot)
+    p.set_option("check_finite", 0)
+    p.set_option("tile_z", 16)
+    dm = torch.tensor(wl.trials, device=dev)
+    if a.profile == "fwd":
+        run = lambda: p.apply_F(dm)
+    else:
+        d = torch.zeros((1, wl.ns, wl.nt, wl.nr), device=dev)
+        d[0, :, :, :] = 1e-3 * torch.randn((wl.ns, wl.nt, wl.nr), device=dev)
+        run = lambda: p.apply_Fadj(d)
+    run()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    run()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": a.profile, "shots": wl.ns, "seconds": time.perf_counter() - t,
+                      "stats": p.stats()}))
+
+
+# ---------------------------------------------------------------------------
+# Oracle (CPU) timing: the reference arm and the cpu_baseline leg
+# ---------------------------------------------------------------------------
+def _oracle_shot(args):
+    cfg, shot, nt_sample = args
+    import numpy as np
+
+    from oracle.wave import Problem
+    from workloads import make_config
+    wl = make_config(cfg)
+    p = Problem(wl.m0, wl.h, wl.dt, nt_sample, wl.pad, wl.src[shot:shot + 1], wl.rec,
+                wl.wavelet[:nt_sample])
+    t = time.perf_counter()
+    p.hessian(wl.trials[0].astype(np.float64))
+    el = time.perf_counter() - t
+    cells = 4.0 * wl.cells_padded() * (nt_sample - 1)     # fwd u0+du, recompute-free history, adjoint
+    return cells, el
+
+
+def oracle_sample(cfg, nshots, nt_sample):
+    """Run the oracle H on `nshots` shots x `nt_sample` steps, one process per shot."""
+    import multiprocessing as mp
+    workers = max(1, min(nshots, os.cpu_count() or 1))
+    ctx = mp.get_context("spawn")
+    t = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        res = pool.map(_oracle_shot, [(cfg, s, nt_sample) for s in range(nshots)])
+    wall = time.perf_counter() - t
+    cells = sum(r[0] for r in res)
+    return cells / wall / 1e9, workers, wall
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    src = os.path.join(ROOT, "paper_1101_3615_gb300", "csrc", "stencil2d.cu")
+    with open(src, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kind):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kind]
+        if e.get("source_sha") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from workloads import CONFIG_NAMES, make_config
+    wl = make_config(a.config)
+    if a.shots:
+        wl.src = wl.src[:a.shots]
+    if a.profile:
+        return profile_run(a, wl)
+    cells_per_h = 4.0 * wl.cells_padded() * (wl.nt - 1) * wl.ns * wl.trials.shape[0]
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        # each step: a bounded sample of the workload (8 shots x 40 steps of H)
+        nsh, nts = min(8, wl.ns), 41
+        vals = []
+        for i in range(a.warmup + a.steps):
+            v, cores, wall = oracle_sample(a.config, nsh, nts)
+            if i >= a.warmup:
+                vals.append((v, wall))
+        value = statistics.median(v for v, _ in vals)
+        ms = statistics.median(w for _, w in vals) * 1e3
+        sample = f"{nsh} shots x {nts - 1} steps of H on the full {wl.padded_shape} grid per step"
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CONFIG_NAMES[a.config], "oracle": "NumPy FP64, one process per shot"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    # CPU baseline first (spawned pool, before any CUDA work), rank 0 at N=1 only
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        nsh, nts = min(16, wl.ns, os.cpu_count() or 1), 101
+        v, cores, wall = oracle_sample(a.config, nsh, nts)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{nsh} shots x {nts - 1} steps of H (F then F*) on the full "
+                         f"{wl.padded_shape[0]}x{wl.padded_shape[1]} padded grid, {wall:.1f} s wall"}
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    if rank == 0:
+        ge._build_module().build()
+    if dist:
+        dist.barrier()
+    from paper_1101_3615_gb300 import Probe
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    p = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet, snapshot_dtype=a.snapshot)
+    p.set_option("check_finite", 0)
+    p.set_option("tile_z", 16)
+    dm = torch.tensor(wl.trials, device=dev)
+    out = torch.empty_like(dm)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(a.warmup):
+        p.apply_H(dm, out=out)
+    torch.cuda.synchronize(dev)
+
+    # timed region: K steps, per-sweep CUDA events recorded by the library
+    p.set_option("timing", 1)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fwd_ms = fwd_b = rec_ms = adj_ms = adj_b = 0.0
+    launches = fwd_l = adj_l = 0
+    for _ in range(a.steps):
+        p.apply_H(dm, out=out)
+        s = p.stats()
+        fwd_ms += s["ms_forward"]
+        fwd_b += s["bytes_forward"]
+        fwd_l += s["launches_forward"]
+        rec_ms += s["ms_recompute"]
+        adj_ms += s["ms_adjoint"]
+        adj_b += s["bytes_adjoint"]
+        adj_l += s["launches_adjoint"]
+        launches += s["launches_total"]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    ms_step = ms_total / a.steps
+    value = cells_per_h * world / (ms_step * 1e-3) / 1e9
+    h_per_s = wl.trials.shape[0] * world / (ms_step * 1e-3)
+    stats = p.stats()
+    p.set_option("timing", 0)
+
+    peak, peak_kind = measured_peaks()
+    fwd_launch_bytes = fwd_b / max(fwd_l, 1)
+    fwd_launch_ms = fwd_ms / max(fwd_l, 1)
+    achieved = fwd_launch_bytes / (fwd_launch_ms * 1e-3) / 1e9
+    adj_achieved = (adj_b / max(adj_l, 1)) / ((adj_ms / max(adj_l, 1)) * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers
+    dm_host = np.ascontiguousarray(wl.trials)
+    out_host = np.empty_like(dm_host)
+    p.apply_H(dm_host, out=out_host)
+    e2e_steps = max(2, min(a.steps, 4))
+    torch.cuda.synchronize(dev)
+    barrier()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        p.apply_H(dm_host, out=out_host)
+    e2e_s = max_over_ranks((time.perf_counter() - t) / e2e_steps)
+    e2e = {"value": cells_per_h * world / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(dm_host.nbytes), "d2h_bytes_per_step": int(out_host.nbytes)}
+
+    # quick FP32 dot-product test on the full workload (stated error)
+    d = p.apply_F(dm)
+    img = p.apply_Fadj(d)
+    lhs = float(torch.sum(d.double() ** 2))
+    rhs = float(torch.sum(dm.double() * img.double()))
+    dot_err = abs(lhs - rhs) / abs(lhs)
+    del d, img
+
+    # plain per-shot FP32 path: one shot resident at a time, no shot grouping
+    plain = None
+    if not a.no_plain:
+        nsub = min(4, wl.ns)
+        pp = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src[:nsub], wl.rec, wl.wavelet)
+        for k, v in (("check_finite", 0), ("shot_wave", 1), ("shot_group", 1), ("tile_z", 16)):
+            pp.set_option(k, v)
+        pp.apply_H(dm, out=out)
+        torch.cuda.synchronize(dev)
+        ep0 = torch.cuda.Event(enable_timing=True)
+        ep1 = torch.cuda.Event(enable_timing=True)
+        ep0.record(stream)
+        pp.apply_H(dm, out=out)
+        ep1.record(stream)
+        torch.cuda.synchronize(dev)
+        per_shot_ms = ep0.elapsed_time(ep1) / nsub
+        plain_ms = per_shot_ms * wl.ns
+        plain = {"value": cells_per_h / (plain_ms * 1e-3) / 1e9, "unit": UNIT,
+                 "h_applies_per_s": wl.trials.shape[0] / (plain_ms * 1e-3),
+                 "ms_per_h": plain_ms,
+                 "how": f"one shot resident at a time, timed on {nsub} shots and scaled to {wl.ns}"}
+        del pp
+
+    traffic = ncu_traffic("fwd_born")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": CONFIG_NAMES[a.config],
+                   "grid_padded": list(wl.padded_shape), "interior": list(wl.shape),
+                   "shots": wl.ns, "trials": int(wl.trials.shape[0]), "nt": wl.nt,
+                   "snapshots": a.snapshot, "ckpt_stride": stats["ckpt_stride"],
+                   "shot_wave": stats["shot_wave"], "shot_group": stats["shot_group"],
+                   "tile_z": stats["tile_z"],
+                   "l2": f"inputs larger than L2: {wl.ns} shots x 4 field planes x "
+                         f"{wl.cells_padded() * 4 / 1e6:.2f} MB = "
+                         f"{wl.ns * 4 * wl.cells_padded() * 4 / 1e6:.0f} MB live state per step "
+                         f"> {L2_BYTES / 1e6:.0f} MB L2; no flush",
+                   "parallelism": f"shots x{world} ranks (independent jobs)"},
+        "h_applies_per_s": h_per_s,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_fwd2d<16, FWD_BORN> (fused incident + Born step)",
+                     "bytes_per_launch": fwd_launch_bytes, "avg_launch_ms": fwd_launch_ms,
+                     "peak_kind": f"{peak_kind} hbm_gbs (copy)"},
+        "adjoint_roofline": {"achieved": adj_achieved, "frac": adj_achieved / peak,
+                             "kernel": "k_adj2d<16,1,kahan> (adjoint step + imaging)"},
+        "sweep_ms_per_step": {"forward": fwd_ms / a.steps, "recompute": rec_ms / a.steps,
+                              "adjoint": adj_ms / a.steps},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "plain": plain,
+        "batched_over_plain": (value / plain["value"]) if plain else None,
+        "stated_error": {"fp32_dot_test": dot_err,
+                         "hv_vs_oracle": "see tests/test_gpu_parity.py (1e-4 FP32, 2e-3 16-bit)"},
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

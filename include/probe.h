@@ -1,0 +1,229 @@
+/*
+ * probe.h -- C ABI of the GB300 matrix-probing library.
+ *
+ * The library applies the wave-equation normal operator H = F*F to batches of
+ * model-space trial functions and fits/applies a pseudodifferential
+ * approximation of its inverse, following Demanet et al., "Matrix probing: a
+ * randomized preconditioner for the wave-equation Hessian":
+ *   - F   Born (linearised) modelling: m0 du_tt - Lap du = -dm (u0)_tt with
+ *         m0 (u0)_tt - Lap u0 = delta(x - s) w(t), data = du at the receivers
+ *         (Sec. 2, the two wave equations and the definition of d(r,s,t));
+ *   - F*  its exact discrete adjoint, reverse-time migration with the zero-lag
+ *         imaging condition (Sec. 1.1, "most accurately computed by
+ *         reverse-time migration");
+ *   - H   = F*F stacked over sources (Sec. 1.1, H = F*F; Sec. 2, the stack
+ *         over sources);
+ *   - fit the randomized least-squares fit of the coefficients c_i of
+ *         H^{-1} = sum_i c_i B_i (Sec. 1.4, Eq. expand and the normal
+ *         equations M c = (Bx)^T y), with B_i the elementary operators of
+ *         Eq. compr2 (Sec. 1.2);
+ *   - precond  sum_i c_i B_i applied to an image (end of Sec. 1.5).
+ *
+ * Discretisation: 2nd order in time, 8th order in space, on the stated grid
+ * (the "interior") surrounded by an absorbing sponge of `pad` cells on every
+ * side; the Laplacian is zero-extended beyond the padded grid.  With
+ * s = dt^2/m0 and a+- = 1 +- eta dt/2 (eta the sponge damping, zero inside):
+ *     u^{n+1} = [2u^n - a- u^{n-1} + s (L u^n + f^n)] / a+ ,  u^{-1} = u^0 = 0,
+ * f^n = w[n] / (h_0 ... h_{d-1}) at the source node, data d^n = R du^n for
+ * n = 0..nt-1 (R = point sampling at receiver nodes).
+ *
+ * Conventions
+ *   - Arrays are C order with the depth axis first: a 2D model-space array is
+ *     [nz][nx], a 3D one [nz][ny][nx]; index tuples are (iz, ix) / (iz, iy, ix)
+ *     into the interior grid.  Model-space vectors live on the interior only.
+ *   - Data arrays are [nb][ns][nt][nr] (receivers fastest).
+ *   - Every array argument may be host or device memory; the library detects
+ *     which (cudaPointerGetAttributes).  The caller owns all I/O buffers.  The
+ *     library owns its workspaces, wavefield checkpoints and captured graphs.
+ *   - Calls enqueue work on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  If any array argument is host memory, or finiteness checking
+ *     is on (the default), the call synchronises `stream` before returning.
+ *   - No exception crosses the ABI.  Every failure returns a probe_status and
+ *     leaves a message retrievable with probe_last_error(); on failure the
+ *     contents of output buffers are unspecified.
+ *   - A handle is not thread-safe: serialise calls on one handle.
+ */
+#ifndef PROBE_H
+#define PROBE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct probe_s* probe_t;              /* opaque, library-owned */
+typedef struct CUstream_st* probe_stream_t;   /* identical to cudaStream_t */
+
+typedef enum {
+    PROBE_OK = 0,
+    PROBE_ERR_ARG = -1,        /* invalid argument (sizes, indices, CFL, pointers) */
+    PROBE_ERR_CUDA = -2,       /* a CUDA runtime / cuFFT call failed */
+    PROBE_ERR_OOM = -3,        /* device allocation failed */
+    PROBE_ERR_TIMEOUT = -4,    /* a bounded device-side wait gave up */
+    PROBE_ERR_NONFINITE = -5,  /* NaN or Inf found in an input or an output */
+    PROBE_ERR_STATE = -6       /* call not valid in the handle's current state */
+} probe_status;
+
+enum { PROBE_SNAP_FP32 = 0, PROBE_SNAP_BF16 = 1, PROBE_SNAP_FP16 = 2 };
+
+/* Grid and numerical options (read once by probe_create). */
+typedef struct {
+    int ndim;            /* 2 or 3 */
+    int n[3];            /* interior size, slowest axis first: {nz, nx} or {nz, ny, nx} */
+    double h[3];         /* grid spacing [m], same order */
+    int pad;             /* absorbing-sponge width in cells, added on every side (>= 0) */
+    int snapshot_dtype;  /* PROBE_SNAP_*: storage type of incident-field checkpoints */
+    int kahan;           /* 1: Kahan-compensated FP32 imaging accumulation, 0: plain FP32 */
+    int ckpt_stride;     /* steps between checkpoints; 0 = ceil(sqrt(nt)) */
+} probe_grid;
+
+/* Description of the elementary operators B_i of the symbol expansion
+ * (Eq. compr2; 3D uses spherical harmonics in angle, Sec. 1.2).  Term
+ * i = (lam * nangular + a) * nradial + q has the symbol
+ *     alpha_lam(x) * A_a(k/|k|) * T_q((|k| - L) / (|k| + L)) * |k|^order
+ * with T_q the Chebyshev polynomial (TL_q are rational Chebyshev functions),
+ * and is applied as B_i x = alpha_lam * IFFT[A_a T_q |k|^order FFT(x)] on the
+ * interior zero-padded by fft_pad cells per side; the k = 0 coefficient maps
+ * to zero.  Real bases: per-axis spatial factor of mode index k on an axis of
+ * n interior cells is 1 (k = 0), cos(2 pi k i / n) (k > 0), sin(2 pi |k| i / n)
+ * (k < 0).  2D angular index q: 1 (q = 0), cos(q theta) (q > 0), sin(|q| theta)
+ * (q < 0), theta = atan2(k_z, k_x).  3D angular index 0..5: 1, kx ky, ky kz,
+ * kx kz, kx^2 - ky^2, 3 kz^2 - 1 of the unit wave vector.  Wave numbers are in
+ * rad/m. */
+typedef struct {
+    int ndim;
+    int nspatial;
+    const int* spatial;  /* [nspatial][ndim] mode indices, host memory */
+    int nangular;
+    const int* angular;  /* [nangular], host memory */
+    int nradial;
+    double L;            /* rational-Chebyshev map scale [rad/m], > 0 */
+    double order;        /* exponent of |k| (-1 for the inverse Hessian, Eq. type10_b) */
+    int fft_pad;         /* >= 0 */
+} probe_basis;
+
+/* Tunables (probe_set_option).  Defaults are chosen by the library. */
+typedef enum {
+    PROBE_OPT_CHECK_FINITE = 1,  /* 1 (default): check inputs/outputs for NaN/Inf, sync */
+    PROBE_OPT_SHOT_WAVE = 2,     /* max shots resident at once; 0 (default) = memory planner */
+    PROBE_OPT_SHOT_GROUP = 3,    /* shots per CTA in the adjoint sweep; 0 = autotuned */
+    PROBE_OPT_USE_GRAPH = 4,     /* 1 (default): replay sweeps from a captured CUDA graph */
+    PROBE_OPT_TIMING = 5,        /* 1: record per-sweep CUDA-event timings (probe_get_stats) */
+    PROBE_OPT_TILE_Z = 6         /* 2D tile height override (8, 16 or 32); 0 = autotuned */
+} probe_option;
+
+/* Counters and timings of the last apply call (probe_get_stats). */
+typedef struct {
+    double ms_forward;           /* forward (incident + Born) sweeps, CUDA events */
+    double ms_recompute;         /* checkpoint recompute sweeps */
+    double ms_adjoint;           /* adjoint + imaging sweeps */
+    double ms_total;             /* whole call on the device */
+    long long launches_forward;  /* kernel launches in each sweep kind */
+    long long launches_recompute;
+    long long launches_adjoint;
+    long long launches_total;    /* every kernel launch of the call */
+    double cell_updates_forward; /* executed stencil cell-updates on the padded grid */
+    double cell_updates_recompute;
+    double cell_updates_adjoint;
+    double bytes_forward;        /* algorithmic HBM bytes of each sweep kind */
+    double bytes_recompute;
+    double bytes_adjoint;
+    int shot_wave;               /* shots resident per wave */
+    int shot_group;              /* shots per CTA in the adjoint */
+    int tile_z;                  /* 2D tile height used */
+    int ckpt_stride;             /* checkpoint spacing used */
+} probe_stats;
+
+/* Create a handle for one background model and acquisition geometry.
+ * m0 [n...] interior slowness squared 1/c^2 (> 0, finite); src_idx [ns][ndim],
+ * rec_idx [nr][ndim] interior node indices (several receivers may share a node);
+ * wavelet [nt] source signature w(n dt) (Sec. 2: f_s = delta(x-s) w(t)).
+ * Fails with PROBE_ERR_ARG on out-of-range indices, non-positive sizes or
+ * spacing, or c_max dt / h_min above the stability limit of the scheme
+ * (0.5547 in 2D, 0.4529 in 3D).  On success *out owns device memory until
+ * probe_destroy. */
+probe_status probe_create(probe_t* out, const probe_grid* grid, const float* m0,
+                          int ns, const int* src_idx, int nr, const int* rec_idx,
+                          const float* wavelet, int nt, double dt);
+
+/* d = F dm: Born data of nb model perturbations (Sec. 2 linearised wave
+ * equation).  dm [nb][n...] (interior), d [nb][ns][nt][nr]. */
+probe_status probe_apply_F(probe_t h, const float* dm, float* d, int nb,
+                           probe_stream_t stream);
+
+/* img = F* d: exact adjoint of probe_apply_F (reverse-time migration, zero-lag
+ * imaging condition, Sec. 1.1).  d [nb][ns][nt][nr], img [nb][n...]. */
+probe_status probe_apply_Fadj(probe_t h, const float* d, float* img, int nb,
+                              probe_stream_t stream);
+
+/* Hdm = F*F dm summed over all shots (Sec. 1.1, H = F*F; Sec. 2 stack over
+ * sources) for a batch of nb trial functions.  dm, Hdm [nb][n...]; may alias. */
+probe_status probe_apply_H(probe_t h, const float* dm, float* Hdm, int nb,
+                           probe_stream_t stream);
+
+/* probe_apply_H on several models (of possibly different grid sizes) at once:
+ * the sweeps of all models advance in the same kernel launches.  All models
+ * must share nt, dt and the checkpoint stride.  dm[k], Hdm[k] are the arrays
+ * of model k with nb[k] trials each.  nmodels <= 4. */
+probe_status probe_apply_H_group(const probe_t* models, int nmodels,
+                                 const float* const* dm, float* const* Hdm,
+                                 const int* nb, probe_stream_t stream);
+
+/* Randomized fit of Sec. 1.4: given trial functions y_j and x_j = H y_j
+ * (j = 1..p, each [n...]), find the coefficients c (FP64, [P] with
+ * P = nspatial * nangular * nradial) minimising
+ *     sum_j || y_j - sum_i c_i B_i x_j ||^2
+ * by the normal equations M c = (Bx)^T y, M_ik = sum_j (B_i x_j)^T (B_k x_j),
+ * formed and solved in FP64 on the device.  coeffs and resid_rel
+ * (||y - Bx c|| / ||y||) are written to host memory; the call synchronises.
+ * Returns PROBE_ERR_STATE if M is not numerically positive definite. */
+probe_status probe_fit(probe_t h, const probe_basis* basis, const float* y,
+                       const float* Hy, int p, double* coeffs, double* resid_rel,
+                       probe_stream_t stream);
+
+/* out = sum_i c_i B_i img (end of Sec. 1.5).  coeffs [P] FP64, img and out
+ * [n...]; img and out may alias. */
+probe_status probe_apply_precond(probe_t h, const probe_basis* basis,
+                                 const double* coeffs, const float* img, float* out,
+                                 probe_stream_t stream);
+
+/* Nonlinear prediction d = calF[m] (Sec. 1.1): the receiver traces of
+ * m u_tt - Lap u = f_s for every shot; m [n...] interior (the sponge keeps the
+ * values of m0), d [ns][nt][nr]. */
+probe_status probe_forward_nonlinear(probe_t h, const float* m, float* d,
+                                     probe_stream_t stream);
+
+/* g = F*[m] resid: migration of the residual with the Born operator
+ * linearised at m (Sec. 1.1: dJ/dm = -F*(d - calF[m]) = F*[m] (calF[m] - d)).
+ * m, g [n...], resid [ns][nt][nr]. */
+probe_status probe_gradient(probe_t h, const float* m, const float* resid, float* g,
+                            probe_stream_t stream);
+
+/* Set a tunable (probe_option); returns PROBE_ERR_ARG for unknown keys or values. */
+probe_status probe_set_option(probe_t h, int key, long long value);
+
+/* Copy the statistics of the last apply call (requires that call's stream to
+ * have completed when timings are enabled). */
+probe_status probe_get_stats(probe_t h, probe_stats* out);
+
+/* Number of interior cells (prod n) and the padded-grid size, for callers
+ * that size their own buffers. */
+probe_status probe_sizes(probe_t h, long long* n_model, long long* n_padded, int* ns,
+                         int* nr, int* nt);
+
+/* Last error message of the handle (or of the last failed probe_create when
+ * h is NULL).  Valid until the next call on the same handle. */
+const char* probe_last_error(probe_t h);
+
+/* Release every resource of the handle (safe on NULL). */
+void probe_destroy(probe_t h);
+
+/* Library version string. */
+const char* probe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROBE_H */

@@ -1,0 +1,107 @@
+// Internal (not ABI) declarations of the matrix-probing library: kernel
+// parameter blocks, the per-model device state and the launcher entry points
+// that the C ABI layer (probe_api.cu) drives.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/probe.h"
+
+namespace probe {
+
+constexpr int kMaxModels = 4;
+constexpr int kTX = 64;        // 2D tile width (x), 16 float4 lanes
+constexpr int kThreads = 256;  // threads per stencil CTA
+constexpr int kMaxNbc = 8;     // trials per adjoint CTA (register accumulators)
+
+// ---------------------------------------------------------------------------
+// Kernel parameter block of one model inside a (possibly multi-model) launch.
+// Passed by value as a __grid_constant__ so the TMA descriptors live in param
+// space.
+// ---------------------------------------------------------------------------
+struct alignas(128) ModelStep2D {
+    CUtensorMap tm_u;  // incident-field planes  [W*2][Nz][P]
+    CUtensorMap tm_f;  // Born / adjoint planes  [W*nb*2][Nz][P]
+    int Nz, Nx, P, pad, nz, nx;
+    int tiles_x, tiles_z, ntiles;
+    int block_begin;   // first linear block index of this model in the launch
+    int nshots;        // shots resident in this launch
+    int nb;            // trials (Born / adjoint fields per shot)
+    int shot_group;    // adjoint: shots handled by one CTA
+    int ngroups;       // adjoint: ceil(nshots / shot_group)
+    int nbc_chunks;    // adjoint: ceil(nb / NBC)
+    int nr;
+    int dtt_slot;      // segment-buffer slot of this step
+    float cz, cx;      // sponge: eta dt/2 = cz rho_z^2 + cx rho_x^2
+    float c0;          // w0 (1/hz^2 + 1/hx^2)
+    float lz[4], lx[4];  // w_k / h^2 per axis, k = 1..4
+    float inv_dt2;
+    float vol_inv;     // 1 / (hz hx)
+    long long F;       // floats per plane (Nz * P)
+    float* u;          // incident state base
+    float* f;          // Born/adjoint state base
+    const float* s;    // dt^2 / m on the padded grid [F]
+    const float* dm;   // [nb][F] model perturbations (zero in the pad)
+    float* dtt;        // segment buffer, Dtt u^n  [W][K][F]
+    long long dtt_shot_stride;
+    const float* wavelet;   // [nt]
+    const int* src_zx;      // [W][2] padded source cell of each resident shot
+    const int* rec_tile_ptr;  // [ntiles + 1]
+    const int* rec_tile_idx;  // receivers sorted by tile
+    const int* rec_zx;        // [nr][2] padded receiver cells
+    float* data;              // forward output traces
+    const float* rdata;       // adjoint input traces
+    long long data_shot_stride, data_trial_stride;  // floats; time stride = nr
+    float* img;               // [ngroups][nb][F]
+    float* comp;              // Kahan compensation, same layout
+    long long img_group_stride;
+};
+
+struct StepParams2D {
+    int nmodels;
+    int n;    // time index of the step (forward: u^n -> u^{n+1}; adjoint: computes mu^n)
+    int nt;
+    int* err; // device error word
+    ModelStep2D m[kMaxModels];
+};
+
+// Launchers (stencil2d.cu).  `blocks` = total blocks over the models.
+enum FwdKind { FWD_INCIDENT = 0, FWD_INCIDENT_DTT = 1, FWD_BORN = 2, FWD_INCIDENT_SAMPLE = 3 };
+cudaError_t launch_fwd2d(FwdKind kind, int tile_z, const StepParams2D& p, int blocks,
+                         cudaStream_t st);
+cudaError_t launch_adj2d(int tile_z, int nbc, bool kahan, const StepParams2D& p, int blocks,
+                         int chunks, cudaStream_t st);
+size_t fwd2d_smem_bytes(FwdKind kind, int tile_z);
+size_t adj2d_smem_bytes(int tile_z);
+cudaError_t stencil2d_configure();  // opt-in shared memory sizes
+
+// Auxiliary kernels (aux.cu).
+cudaError_t launch_embed(const float* src_int, float* dst_pad, int nb, int nz, int nx, int ny,
+                         int pad, int Nz, int Nx, int Ny, int P, long long F, float scale,
+                         cudaStream_t st);
+cudaError_t launch_make_s(const float* m_int, const float* m0_int, float* s_pad, int nz, int ny,
+                          int nx, int pad, int P, long long F, int Nz, int Ny, int Nx, float dt2,
+                          cudaStream_t st);
+cudaError_t launch_extract_images(const float* img, const float* comp, int ngroups,
+                                  long long group_stride, int nb, long long F, float* out,
+                                  int nz, int ny, int nx, int pad, int Ny, int P, bool kahan,
+                                  bool accumulate, cudaStream_t st);
+cudaError_t launch_sample(const float* field, long long plane_stride_shot,
+                          long long plane_stride_trial, int plane, long long F, int nshots,
+                          int nb, const int* rec_zx, int nr, int P, int ndim, int Ny, float* data,
+                          long long data_shot_stride, long long data_trial_stride, int n,
+                          cudaStream_t st);
+cudaError_t launch_check_finite(const float* a, long long n, int* err, cudaStream_t st);
+// pc = plane parity of u^n (u^{n-1} is in the other plane of each shot).
+cudaError_t launch_encode_ckpt(const float* state, int nplanes, long long F, int pc, void* dst,
+                               float* scales, int dtype, float* absmax_scratch, cudaStream_t st);
+cudaError_t launch_decode_ckpt(const void* src, const float* scales, int nplanes, long long F,
+                               int pc, int dtype, float* state, cudaStream_t st);
+cudaError_t launch_scale_copy(const float* src, float* dst, long long n, float a, cudaStream_t st);
+
+}  // namespace probe

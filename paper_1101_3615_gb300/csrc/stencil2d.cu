@@ -1,0 +1,502 @@
+// 2D time-stepping kernels of the Born / migration sweeps (sm_103a).
+//
+// One launch advances every resident (model, shot) by one time step.  A CTA of
+// 256 threads owns a 64 x TZ tile of one shot; the radius-4 halo tile of the
+// field being differentiated is staged in shared memory by a TMA tiled load
+// (cp.async.bulk.tensor, zero fill outside the padded grid = the zero
+// extension of the Laplacian), the pointwise operands (previous level, s, dm,
+// Dtt u) stream through coalesced float4 loads, and each thread updates 4
+// consecutive x cells per row.  The sponge factors are computed from the cell
+// index, the point source and the receivers are handled inside the tile.
+//
+// Scheme (Sec. 2 wave equations, 2nd order in time / 8th order in space):
+//   u^{n+1}  = G [2u^n  - a- u^{n-1}  + s (L u^n + f^n)]
+//   du^{n+1} = G [2du^n - a- du^{n-1} + s (L du^n - dm Dtt u^n)],
+//   Dtt u^n  = s (L u^n + f^n) / dt^2   (exact in the interior, where dm lives)
+// Adjoint (exact transpose, written for the scaled variable mu = s G lambda,
+// which obeys the same recurrence run backwards in time):
+//   mu^n = G [2mu^{n+1} - a- mu^{n+2} + s (L mu^{n+1} + R^T r^n)]
+//   img -= Dtt u^{n-1} * mu^n                 (zero-lag imaging, Sec. 1.1 RTM)
+#include "common.cuh"
+#include "internal.h"
+
+namespace probe {
+
+template <int TZ>
+struct Tile2D {
+    static constexpr int HX = kTX + 8;
+    static constexpr int HZ = TZ + 8;
+    static constexpr int FLOATS = HX * HZ;
+    static constexpr unsigned BYTES = FLOATS * 4u;
+    static constexpr int ROWS = TZ / 16;
+};
+
+__device__ __forceinline__ int find_model(const StepParams2D& p, int blk) {
+    int mi = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxModels; ++k)
+        if (k < p.nmodels && blk >= p.m[k].block_begin) mi = k;
+    return mi;
+}
+
+// Laplacian of the 4 cells starting at tile coordinates (row, col) (col % 4 == 0).
+// Each tap pair is accumulated as (u[+k] - u) + (u[-k] - u): since the weights
+// satisfy w0 = -2 sum_k w_k this equals w0 u + sum_k w_k (u[+k] + u[-k]), but the
+// differences of neighbouring values are nearly exact in FP32, which removes the
+// cancellation between the centre term and the neighbour sums (the dominant
+// round-off of the time stepping for smooth, well-sampled fields).
+template <int HX>
+__device__ __forceinline__ void lap4(const float* t, int row, int col, const ModelStep2D& M,
+                                     float4& center, float L[4]) {
+    const float* rp = t + row * HX + col;
+    const float4 a = ld4(rp - 4), b = ld4(rp), c = ld4(rp + 4);
+    const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    center = b;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float u0 = v[4 + j];
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) acc = fmaf(M.lx[k - 1], (v[4 + j + k] - u0) + (v[4 + j - k] - u0), acc);
+        L[j] = acc;
+    }
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        const float4 up = ld4(rp - k * HX), dn = ld4(rp + k * HX);
+        const float w = M.lz[k - 1];
+        L[0] = fmaf(w, (up.x - b.x) + (dn.x - b.x), L[0]);
+        L[1] = fmaf(w, (up.y - b.y) + (dn.y - b.y), L[1]);
+        L[2] = fmaf(w, (up.z - b.z) + (dn.z - b.z), L[2]);
+        L[3] = fmaf(w, (up.w - b.w) + (dn.w - b.w), L[3]);
+    }
+}
+
+// Sponge term e = eta dt / 2 of a padded cell (zero in the interior).
+__device__ __forceinline__ float sponge_e(const ModelStep2D& M, int z, int x) {
+    const int rz = max(max(M.pad - z, z - (M.pad + M.nz - 1)), 0);
+    const int rx = max(max(M.pad - x, x - (M.pad + M.nx - 1)), 0);
+    return M.cz * (float)(rz * rz) + M.cx * (float)(rx * rx);
+}
+
+// Record the receivers of this tile from a staged field tile.
+template <int HX>
+__device__ __forceinline__ void sample_tile(const float* t, const ModelStep2D& M, int tile, int z0,
+                                            int x0, float* out) {
+    const int beg = M.rec_tile_ptr[tile], end = M.rec_tile_ptr[tile + 1];
+    for (int i = beg + (int)threadIdx.x; i < end; i += kThreads) {
+        const int r = M.rec_tile_idx[i];
+        const int rz = M.rec_zx[2 * r], rx = M.rec_zx[2 * r + 1];
+        out[r] = t[(rz - z0 + 4) * HX + (rx - x0 + 4)];
+    }
+}
+
+// After a failed bounded wait: flag the error and give the copies in flight
+// one more bounded wait before the CTA releases its shared memory.
+__device__ __forceinline__ void abort_cta(int* err, uint64_t* bars, int nbars,
+                                          const uint32_t* parity) {
+    if (threadIdx.x == 0) {
+        set_dev_error(err, DEVERR_TIMEOUT);
+        for (int i = 0; i < nbars; ++i) (void)mbar_wait_bounded(&bars[i], parity[i]);
+    }
+}
+
+template <int TZ, int KIND>
+__global__ void __launch_bounds__(kThreads) k_fwd2d(const __grid_constant__ StepParams2D p) {
+    using T = Tile2D<TZ>;
+    constexpr int HX = T::HX;
+    constexpr int ROWS = T::ROWS;
+    constexpr bool BORN = (KIND == FWD_BORN);
+    constexpr bool DTT = (KIND == FWD_INCIDENT_DTT);
+    constexpr bool SAMPLE_U = (KIND == FWD_INCIDENT_SAMPLE);
+
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bars[3];
+
+    const int mi = find_model(p, blockIdx.x);
+    const ModelStep2D& M = p.m[mi];
+    const int blk = blockIdx.x - M.block_begin;
+    const int shot = blk / M.ntiles;
+    const int tile = blk - shot * M.ntiles;
+    const int tzi = tile / M.tiles_x;
+    const int z0 = tzi * TZ, x0 = (tile - tzi * M.tiles_x) * kTX;
+    const int tid = threadIdx.x;
+    const int lx = (tid & 15) << 2, lz = tid >> 4;
+    const int n = p.n;
+    const int pc = n & 1, po = pc ^ 1;
+    const long long F = M.F;
+    float* su = smem;
+    float* sf0 = smem + T::FLOATS;
+    float* sf1 = smem + 2 * T::FLOATS;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(&bars[0], T::BYTES);
+        tma_load_3d(su, &M.tm_u, x0 - 4, z0 - 4, shot * 2 + pc, &bars[0]);
+        if (BORN && M.nb > 0) {
+            mbar_expect_tx(&bars[1], T::BYTES);
+            tma_load_3d(sf0, &M.tm_f, x0 - 4, z0 - 4, (shot * M.nb) * 2 + pc, &bars[1]);
+        }
+    }
+
+    const int x = x0 + lx;
+    float* ubase = M.u + (long long)(shot * 2) * F;
+    float4 sv[ROWS], uo[ROWS];
+    long long off[ROWS];
+    bool valid[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int z = z0 + lz + 16 * r;
+        valid[r] = (z < M.Nz) && (x < M.Nx);
+        off[r] = (long long)z * M.P + x;
+        sv[r] = valid[r] ? ld4(M.s + off[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        uo[r] = valid[r] ? ld4(ubase + po * F + off[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+
+    const uint32_t par0[3] = {0u, 0u, 0u};
+    const bool ok0 = mbar_wait_bounded(&bars[0], 0);
+    if (__syncthreads_or(!ok0)) {
+        abort_cta(p.err, bars, BORN && M.nb > 0 ? 2 : 1, par0);
+        return;
+    }
+
+    const int sz = M.src_zx[2 * shot], sx = M.src_zx[2 * shot + 1];
+    const float fsrc = M.wavelet[n] * M.vol_inv;
+    float D[ROWS][4], Gc[ROWS][4], Am[ROWS][4];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int z = z0 + lz + 16 * r;
+        float L[4];
+        float4 c;
+        lap4<HX>(su, lz + 16 * r + 4, lx + 4, M, c, L);
+        if (z == sz) {
+            const int j = sx - x;
+            if (j >= 0 && j < 4) L[j] += fsrc;
+        }
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float Fo = get(sv[r], j) * L[j];
+            D[r][j] = Fo * M.inv_dt2;
+            const float e = sponge_e(M, z, x + j);
+            float G = 1.f, am = 1.f;
+            if (e != 0.f) {
+                G = __frcp_rn(1.f + e);
+                am = 1.f - e;
+            }
+            Gc[r][j] = G;
+            Am[r][j] = am;
+            o[j] = (x + j < M.Nx) ? G * (2.f * get(c, j) - am * get(uo[r], j) + Fo) : 0.f;
+        }
+        if (valid[r]) {
+            st4(ubase + po * F + off[r], make_float4(o[0], o[1], o[2], o[3]));
+            if (DTT)
+                st4(M.dtt + (long long)shot * M.dtt_shot_stride + (long long)M.dtt_slot * F + off[r],
+                    make_float4(D[r][0], D[r][1], D[r][2], D[r][3]));
+        }
+    }
+    if (SAMPLE_U)
+        sample_tile<HX>(su, M, tile, z0, x0, M.data + (long long)shot * M.data_shot_stride +
+                                                 (long long)n * M.nr);
+
+    if (BORN) {
+        const int nb = M.nb;
+        for (int b = 0; b < nb; ++b) {
+            const int buf = b & 1;
+            float* sf = buf ? sf1 : sf0;
+            if (tid == 0 && b + 1 < nb) {
+                mbar_expect_tx(&bars[1 + (buf ^ 1)], T::BYTES);
+                tma_load_3d(buf ? sf0 : sf1, &M.tm_f, x0 - 4, z0 - 4, ((shot * nb + b + 1) * 2) + pc,
+                            &bars[1 + (buf ^ 1)]);
+            }
+            float* fb = M.f + (long long)((shot * nb + b) * 2) * F;
+            const float* dmb = M.dm + (long long)b * F;
+            float4 dv[ROWS], fo[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                dv[r] = valid[r] ? ld4(dmb + off[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                fo[r] = valid[r] ? ld4(fb + po * F + off[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            const bool ok = mbar_wait_bounded(&bars[1 + buf], (b >> 1) & 1);
+            if (__syncthreads_or(!ok)) {
+                const uint32_t par[3] = {0u, (uint32_t)((b >> 1) & 1), (uint32_t)((b >> 1) & 1)};
+                abort_cta(p.err, bars + 1 + buf, 1, par + 1 + buf);
+                return;
+            }
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                float L[4];
+                float4 c;
+                lap4<HX>(sf, lz + 16 * r + 4, lx + 4, M, c, L);
+                float o[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float src = L[j] - get(dv[r], j) * D[r][j];
+                    o[j] = (x + j < M.Nx) ? Gc[r][j] * (2.f * get(c, j) - Am[r][j] * get(fo[r], j) +
+                                                        get(sv[r], j) * src)
+                                          : 0.f;
+                }
+                if (valid[r]) st4(fb + po * F + off[r], make_float4(o[0], o[1], o[2], o[3]));
+            }
+            sample_tile<HX>(sf, M, tile, z0, x0,
+                            M.data + (long long)shot * M.data_shot_stride +
+                                (long long)b * M.data_trial_stride + (long long)n * M.nr);
+            __syncthreads();
+        }
+    }
+}
+
+template <int TZ, int NBC, bool KAHAN>
+__global__ void __launch_bounds__(kThreads) k_adj2d(const __grid_constant__ StepParams2D p) {
+    using T = Tile2D<TZ>;
+    constexpr int HX = T::HX;
+    constexpr int ROWS = T::ROWS;
+
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+
+    const int mi = find_model(p, blockIdx.x);
+    const ModelStep2D& M = p.m[mi];
+    const int blk = blockIdx.x - M.block_begin;
+    const int grp = blk / M.ntiles;
+    const int tile = blk - grp * M.ntiles;
+    const int tzi = tile / M.tiles_x;
+    const int z0 = tzi * TZ, x0 = (tile - tzi * M.tiles_x) * kTX;
+    const int tid = threadIdx.x;
+    const int lx = (tid & 15) << 2, lz = tid >> 4;
+    const int n = p.n;
+    const int pc = (n + 1) & 1;  // plane of mu^{n+1}
+    const int po = n & 1;        // plane of mu^{n+2}, overwritten by mu^n
+    const long long F = M.F;
+    const int nb = M.nb;
+    const int b0 = blockIdx.y * NBC;
+    if (b0 >= nb) return;
+    const int nbc = min(NBC, nb - b0);
+    const int j0 = grp * M.shot_group;
+    const int nsh = min(M.shot_group, M.nshots - j0);
+    const int niter = nsh * nbc;
+    float* sbuf[2] = {smem, smem + T::FLOATS};
+    float* sinj = smem + 2 * T::FLOATS;  // TZ x 64 receiver injection
+
+    const int rbeg = M.rec_tile_ptr[tile], rend = M.rec_tile_ptr[tile + 1];
+    const bool has_rec = rend > rbeg;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0 && niter > 0) {
+        mbar_expect_tx(&bars[0], T::BYTES);
+        tma_load_3d(sbuf[0], &M.tm_f, x0 - 4, z0 - 4, ((j0 * nb + b0) * 2) + pc, &bars[0]);
+    }
+
+    const int x = x0 + lx;
+    float4 sv[ROWS];
+    long long off[ROWS];
+    bool valid[ROWS];
+    float Gc[ROWS][4], Am[ROWS][4];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int z = z0 + lz + 16 * r;
+        valid[r] = (z < M.Nz) && (x < M.Nx);
+        off[r] = (long long)z * M.P + x;
+        sv[r] = valid[r] ? ld4(M.s + off[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float e = sponge_e(M, z, x + j);
+            Gc[r][j] = 1.f;
+            Am[r][j] = 1.f;
+            if (e != 0.f) {
+                Gc[r][j] = __frcp_rn(1.f + e);
+                Am[r][j] = 1.f - e;
+            }
+        }
+    }
+
+    float acc[NBC][ROWS][4];
+#pragma unroll
+    for (int bi = 0; bi < NBC; ++bi)
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[bi][r][j] = 0.f;
+
+    for (int jj = 0; jj < nsh; ++jj) {
+        const int shot = j0 + jj;
+        float4 Dv[ROWS];
+        const float* dtt = M.dtt + (long long)shot * M.dtt_shot_stride + (long long)M.dtt_slot * F;
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r)
+            Dv[r] = valid[r] ? ld4(dtt + off[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int bi = 0; bi < NBC; ++bi) {
+            if (bi < nbc) {
+                const int it = jj * nbc + bi;
+                const int buf = it & 1;
+                const int b = b0 + bi;
+                if (tid == 0 && it + 1 < niter) {
+                    const int jn = j0 + (it + 1) / nbc, bn = b0 + (it + 1) % nbc;
+                    mbar_expect_tx(&bars[buf ^ 1], T::BYTES);
+                    tma_load_3d(sbuf[buf ^ 1], &M.tm_f, x0 - 4, z0 - 4, ((jn * nb + bn) * 2) + pc,
+                                &bars[buf ^ 1]);
+                }
+                float* fb = M.f + (long long)((shot * nb + b) * 2) * F;
+                float4 mo[ROWS];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r)
+                    mo[r] = valid[r] ? ld4(fb + po * F + off[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (has_rec) {
+                    for (int i = tid; i < TZ * kTX; i += kThreads) sinj[i] = 0.f;
+                    __syncthreads();
+                    const float* rr = M.rdata + (long long)shot * M.data_shot_stride +
+                                      (long long)b * M.data_trial_stride + (long long)n * M.nr;
+                    for (int i = rbeg + tid; i < rend; i += kThreads) {
+                        const int rcv = M.rec_tile_idx[i];
+                        atomicAdd(&sinj[(M.rec_zx[2 * rcv] - z0) * kTX + (M.rec_zx[2 * rcv + 1] - x0)],
+                                  rr[rcv]);
+                    }
+                }
+                const bool ok = mbar_wait_bounded(&bars[buf], (it >> 1) & 1);
+                if (__syncthreads_or(!ok)) {
+                    const uint32_t par = (uint32_t)((it >> 1) & 1);
+                    abort_cta(p.err, &bars[buf], 1, &par);
+                    return;
+                }
+                const float* sf = sbuf[buf];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    float L[4];
+                    float4 c;
+                    lap4<HX>(sf, lz + 16 * r + 4, lx + 4, M, c, L);
+                    if (has_rec) {
+                        const float4 iv = ld4(sinj + (lz + 16 * r) * kTX + lx);
+                        L[0] += iv.x;
+                        L[1] += iv.y;
+                        L[2] += iv.z;
+                        L[3] += iv.w;
+                    }
+                    float o[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        o[j] = (x + j < M.Nx) ? Gc[r][j] * (2.f * get(c, j) - Am[r][j] * get(mo[r], j) +
+                                                            get(sv[r], j) * L[j])
+                                              : 0.f;
+                        acc[bi][r][j] = fmaf(-get(Dv[r], j), o[j], acc[bi][r][j]);
+                    }
+                    if (valid[r]) st4(fb + po * F + off[r], make_float4(o[0], o[1], o[2], o[3]));
+                }
+                __syncthreads();
+            }
+        }
+    }
+
+    float* img = M.img + (long long)grp * M.img_group_stride;
+    float* cmp = M.comp + (long long)grp * M.img_group_stride;
+#pragma unroll
+    for (int bi = 0; bi < NBC; ++bi) {
+        if (bi < nbc) {
+            const long long boff = (long long)(b0 + bi) * F;
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                if (!valid[r]) continue;
+                float* ip = img + boff + off[r];
+                float4 iv = ld4(ip);
+                if (KAHAN) {
+                    float* cp = cmp + boff + off[r];
+                    float4 cv = ld4(cp);
+                    float* ia = reinterpret_cast<float*>(&iv);
+                    float* ca = reinterpret_cast<float*>(&cv);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float y = acc[bi][r][j] - ca[j];
+                        const float t = ia[j] + y;
+                        ca[j] = (t - ia[j]) - y;
+                        ia[j] = t;
+                    }
+                    st4(cp, cv);
+                } else {
+                    iv.x += acc[bi][r][0];
+                    iv.y += acc[bi][r][1];
+                    iv.z += acc[bi][r][2];
+                    iv.w += acc[bi][r][3];
+                }
+                st4(ip, iv);
+            }
+        }
+    }
+}
+
+size_t fwd2d_smem_bytes(FwdKind kind, int tile_z) {
+    const size_t tile = (size_t)(kTX + 8) * (tile_z + 8) * 4;
+    return kind == FWD_BORN ? 3 * tile : tile;
+}
+
+size_t adj2d_smem_bytes(int tile_z) {
+    const size_t tile = (size_t)(kTX + 8) * (tile_z + 8) * 4;
+    return 2 * tile + (size_t)tile_z * kTX * 4;
+}
+
+template <int TZ>
+static cudaError_t launch_fwd_tz(FwdKind kind, const StepParams2D& p, int blocks, cudaStream_t st) {
+    const size_t sm = fwd2d_smem_bytes(kind, TZ);
+    switch (kind) {
+        case FWD_INCIDENT: k_fwd2d<TZ, FWD_INCIDENT><<<blocks, kThreads, sm, st>>>(p); break;
+        case FWD_INCIDENT_DTT: k_fwd2d<TZ, FWD_INCIDENT_DTT><<<blocks, kThreads, sm, st>>>(p); break;
+        case FWD_BORN: k_fwd2d<TZ, FWD_BORN><<<blocks, kThreads, sm, st>>>(p); break;
+        case FWD_INCIDENT_SAMPLE:
+            k_fwd2d<TZ, FWD_INCIDENT_SAMPLE><<<blocks, kThreads, sm, st>>>(p);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd2d(FwdKind kind, int tile_z, const StepParams2D& p, int blocks,
+                         cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    if (tile_z == 16) return launch_fwd_tz<16>(kind, p, blocks, st);
+    if (tile_z == 32) return launch_fwd_tz<32>(kind, p, blocks, st);
+    return cudaErrorInvalidValue;
+}
+
+template <int TZ, int NBC>
+static cudaError_t launch_adj_nbc(bool kahan, const StepParams2D& p, int blocks, int chunks,
+                                  cudaStream_t st) {
+    const size_t sm = adj2d_smem_bytes(TZ);
+    dim3 grid(blocks, chunks);
+    if (kahan)
+        k_adj2d<TZ, NBC, true><<<grid, kThreads, sm, st>>>(p);
+    else
+        k_adj2d<TZ, NBC, false><<<grid, kThreads, sm, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int TZ>
+static cudaError_t launch_adj_tz(int nbc, bool kahan, const StepParams2D& p, int blocks, int chunks,
+                                 cudaStream_t st) {
+    switch (nbc) {
+        case 1: return launch_adj_nbc<TZ, 1>(kahan, p, blocks, chunks, st);
+        case 2: return launch_adj_nbc<TZ, 2>(kahan, p, blocks, chunks, st);
+        case 4: return launch_adj_nbc<TZ, 4>(kahan, p, blocks, chunks, st);
+        case 8: return launch_adj_nbc<TZ, 8>(kahan, p, blocks, chunks, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adj2d(int tile_z, int nbc, bool kahan, const StepParams2D& p, int blocks,
+                         int chunks, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    if (tile_z == 16) return launch_adj_tz<16>(nbc, kahan, p, blocks, chunks, st);
+    if (tile_z == 32) return launch_adj_tz<32>(nbc, kahan, p, blocks, chunks, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t stencil2d_configure() { return cudaSuccess; }
+
+}  // namespace probe
