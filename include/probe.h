@@ -200,6 +200,25 @@ probe_status probe_forward_nonlinear(probe_t h, const float* m, float* d,
 probe_status probe_gradient(probe_t h, const float* m, const float* resid, float* g,
                             probe_stream_t stream);
 
+/* probe_apply_F without allocating: the same Born data as probe_apply_F, for
+ * callers that must not allocate device memory during the call (a service that
+ * has handed its remaining memory to its own pool, a framework that forbids
+ * cudaMalloc/cudaFree between its own allocation points because they
+ * synchronise the device, a real-time loop).  This operation has no
+ * counterpart in the paper; it is an engineering variant of probe_apply_F.
+ * Create the handle once beforehand (probe_create allocates its model arrays).
+ * dm [nb][n...] and d [nb][ns][nt][nr] must be device arrays.  The per-call
+ * scratch is a library-internal static device array of 32 MiB, held on every
+ * GPU that loads the library until the process exits; shots are processed in
+ * waves that fit in it, and a call whose single shot does not fit
+ * ((2 + 3 nb) padded planes of 4-byte cells) fails with PROBE_ERR_ARG.  The first
+ * call on a device looks up the array's device address; make that call before
+ * any stream capture.  All calls share the array: calls whose work overlaps on
+ * the GPU race and must be serialised by the caller.  No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+probe_status probe_apply_F_noalloc(probe_t h, const float* dm, float* d, int nb,
+                                   probe_stream_t stream);
+
 /* Set a tunable (probe_option); returns PROBE_ERR_ARG for unknown keys or values. */
 probe_status probe_set_option(probe_t h, int key, long long value);
 

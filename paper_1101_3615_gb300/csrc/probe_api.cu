@@ -1108,3 +1108,152 @@ extern "C" probe_status probe_fit(probe_t h, const probe_basis* basis, const flo
                                   double* coeffs, double* resid_rel, probe_stream_t stream);
 extern "C" probe_status probe_apply_precond(probe_t h, const probe_basis* basis, const double* coeffs,
                                             const float* img, float* out, probe_stream_t stream);
+
+// ---------------------------------------------------------------------------
+// Allocation-free Born forward (probe_apply_F_noalloc).
+//
+// For callers that must not allocate device memory while they run -- code
+// inside a region that owns a fixed, pre-reserved memory budget (an inference
+// or imaging service that hands all remaining memory to its own pool), hosts
+// whose framework forbids cudaMalloc/cudaFree between its own allocation
+// points because they synchronise the device, or real-time loops that cannot
+// afford allocation latency.  Such a caller creates the handle once at set-up
+// time and then calls this entry point, which needs no memory beyond the
+// caller's input and output arrays and the file-scope scratch array below.
+//
+// The scratch is a static __device__ array of kNoAllocScratchBytes (32 MiB);
+// every GPU on which the library is loaded holds it until the process exits.
+// Host code may not use the array's name as a device address, so the first
+// call on each device looks its address up with cudaGetSymbolAddress (with
+// that device current) and caches it; make that first call before any stream
+// capture.  All calls share the array and it keeps the last call's contents:
+// the state planes are cleared at the start of every wave.  Two calls whose
+// work overlaps on the GPU (different streams, or different handles on the
+// same device) race on the scratch and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 32u << 20;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+probe_status noalloc_scratch(probe_t h, void** out) {
+    int devid = 0;
+    CK(h, cudaGetDevice(&devid));
+    if (devid < 0 || devid >= kNoAllocMaxDevices)
+        return fail(h, PROBE_ERR_ARG, "device ordinal beyond the allocation-free path's table");
+    if (!g_noalloc_addr[devid]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(h, e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_addr[devid] = p;
+    }
+    *out = g_noalloc_addr[devid];
+    return PROBE_OK;
+}
+
+}  // namespace
+
+extern "C" probe_status probe_apply_F_noalloc(probe_t h, const float* dm, float* d, int nb,
+                                              probe_stream_t stream) {
+    if (!h) return PROBE_ERR_ARG;
+    if (nb < 0) return fail(h, PROBE_ERR_ARG, "nb must be >= 0");
+    if (nb == 0) return PROBE_OK;
+    if (!dm || !d) return fail(h, PROBE_ERR_ARG, "NULL array");
+    if (h->ndim != 2) return fail(h, PROBE_ERR_ARG, "the allocation-free path handles 2D grids");
+    // per resident shot: incident (2 planes) + nb Born fields (2 planes each); plus nb dm planes
+    const size_t plane = (size_t)h->F * 4;
+    const size_t fixed = (size_t)nb * plane;
+    const size_t per_shot = (size_t)(2 + 2 * nb) * plane;
+    if (fixed + per_shot > kNoAllocScratchBytes) {
+        char buf[200];
+        snprintf(buf, sizeof buf,
+                 "sizes beyond the allocation-free maximum: one shot with nb=%d needs %zu bytes of "
+                 "scratch, the static scratch holds %zu",
+                 nb, fixed + per_shot, kNoAllocScratchBytes);
+        return fail(h, PROBE_ERR_ARG, buf);
+    }
+    if (!is_device_ptr(dm) || !is_device_ptr(d))
+        return fail(h, PROBE_ERR_ARG, "the allocation-free path needs device arrays");
+    cudaStream_t st = (cudaStream_t)stream;
+    void* base = nullptr;
+    TRY(noalloc_scratch(h, &base));
+    const int W = (int)std::min<size_t>((size_t)h->ns, (kNoAllocScratchBytes - fixed) / per_shot);
+    float* s_dm = (float*)base;
+    float* s_u = s_dm + (size_t)nb * h->F;
+    float* s_f = s_u + (size_t)W * 2 * h->F;
+    CUtensorMap tm_u, tm_f;
+    TRY(encode_planes(h, &tm_u, s_u, W * 2, h->tile_z));
+    TRY(encode_planes(h, &tm_f, s_f, W * nb * 2, h->tile_z));
+
+    CK(h, cudaMemsetAsync(s_dm, 0, (size_t)nb * plane, st));
+    cudaError_t e = launch_embed(dm, s_dm, nb, h->nz, h->nx, 1, h->pad, h->Nz, h->Nx, 1, h->P, h->F, 1.0f, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "embed dm");
+
+    const long long tr = (long long)h->nt * h->nr;
+    StepParams2D p;
+    memset(&p, 0, sizeof(p));
+    p.nmodels = 1;
+    p.nt = h->nt;
+    p.err = h->d_err;
+    ModelStep2D& m = p.m[0];
+    m.tm_u = tm_u;
+    m.tm_f = tm_f;
+    m.Nz = h->Nz;
+    m.Nx = h->Nx;
+    m.P = h->P;
+    m.pad = h->pad;
+    m.nz = h->nz;
+    m.nx = h->nx;
+    m.tiles_x = h->tiles_x;
+    m.tiles_z = h->tiles_z;
+    m.ntiles = h->ntiles;
+    m.block_begin = 0;
+    m.nb = nb;
+    m.shot_group = 1;
+    m.ngroups = 1;
+    m.nbc_chunks = 1;
+    m.nr = h->nr;
+    m.cz = h->cz;
+    m.cx = h->cx;
+    const double wk[4] = {PROBE_W1, PROBE_W2, PROBE_W3, PROBE_W4};
+    m.c0 = (float)(PROBE_W0 / (h->hz * h->hz) + PROBE_W0 / (h->hx * h->hx));
+    for (int k = 0; k < 4; ++k) {
+        m.lz[k] = (float)(wk[k] / (h->hz * h->hz));
+        m.lx[k] = (float)(wk[k] / (h->hx * h->hx));
+    }
+    m.inv_dt2 = (float)(1.0 / (h->dt * h->dt));
+    m.vol_inv = (float)(1.0 / (h->hz * h->hx));
+    m.F = h->F;
+    m.u = s_u;
+    m.f = s_f;
+    m.s = h->d_s0;
+    m.dm = s_dm;
+    m.wavelet = h->d_wavelet;
+    m.rec_tile_ptr = h->d_rec_tile_ptr;
+    m.rec_tile_idx = h->d_rec_tile_idx;
+    m.rec_zx = h->d_rec;
+    m.data_shot_stride = tr;
+    m.data_trial_stride = (long long)h->ns * tr;
+
+    for (int j0 = 0; j0 < h->ns; j0 += W) {
+        const int Wv = std::min(W, h->ns - j0);
+        CK(h, cudaMemsetAsync(s_u, 0, (size_t)Wv * 2 * plane, st));
+        CK(h, cudaMemsetAsync(s_f, 0, (size_t)Wv * nb * 2 * plane, st));
+        m.nshots = Wv;
+        m.src_zx = h->d_src + 2 * j0;
+        m.data = d + (long long)j0 * tr;
+        for (int n = 0; n < h->nt - 1; ++n) {
+            p.n = n;
+            e = launch_fwd2d(FWD_BORN, h->tile_z, p, Wv * h->ntiles, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "forward step launch");
+        }
+        e = launch_sample(s_f, (long long)nb * 2 * h->F, 2 * h->F, (h->nt - 1) & 1, h->F, Wv, nb, h->d_rec, h->nr,
+                          h->P, 2, 1, m.data, tr, (long long)h->ns * tr, h->nt - 1, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "receiver sampling");
+    }
+    return finish_call(h, st, false, d, (long long)nb * h->ns * tr);
+}
