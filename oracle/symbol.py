@@ -20,7 +20,10 @@ functions 1 | cos(q theta) | sin(|q| theta) with theta = atan2(k_z, k_x);
 3D angular functions the real l = 0, 2 harmonics
 {1, kx ky, ky kz, kx kz, kx^2 - ky^2, 3 kz^2 - 1} of the unit wave vector;
 TL_q(|k|) = T_q((|k| - L)/(|k| + L)) (rational Chebyshev functions); every
-term maps the k = 0 coefficient to zero.  Term index i = (lam*NA + a)*NQ + q.
+term maps the k = 0 coefficient to zero, and also the Nyquist bins of
+even-length FFT axes (such a bin is its own negative wave vector, where the
+odd angular factors cannot be made even, so no real-to-real operator can use
+them).  Term index i = (lam*NA + a)*NQ + q.
 """
 from __future__ import annotations
 
@@ -94,12 +97,23 @@ class Basis:
                  4: kx ** 2 - ky ** 2, 5: 3.0 * kz ** 2 - 1.0}
         return table[q]
 
+    def _nyquist_mask(self):
+        """True on the Nyquist bins of even-length axes (rfft grid)."""
+        m = np.zeros(tuple(N if ax < self.ndim - 1 else N // 2 + 1
+                           for ax, N in enumerate(self.fshape)), dtype=bool)
+        for ax, N in enumerate(self.fshape):
+            if N % 2 == 0:
+                idx = [slice(None)] * self.ndim
+                idx[ax] = N // 2
+                m[tuple(idx)] = True
+        return m
+
     def multiplier(self, a, q):
-        """beta(k) = A_a(theta) T_q((|k|-L)/(|k|+L)) |k|^e, zero at k = 0."""
+        """beta(k) = A_a(theta) T_q((|k|-L)/(|k|+L)) |k|^e, zero at k = 0 and on Nyquist bins."""
         kvec = self._kgrid()
         knorm = np.sqrt(sum(k ** 2 for k in kvec))
-        pos = knorm > 0
-        safe = np.where(pos, knorm, 1.0)
+        pos = (knorm > 0) & ~self._nyquist_mask()
+        safe = np.where(knorm > 0, knorm, 1.0)
         t = (safe - self.L) / (safe + self.L)
         cheb = np.cos(q * np.arccos(np.clip(t, -1.0, 1.0)))
         beta = self.angular_fn(a, kvec) * cheb * safe ** self.order

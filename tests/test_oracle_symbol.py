@@ -105,3 +105,30 @@ def test_qr_solution_equals_closed_form():
     assert np.linalg.norm(c_qr - c_ne) / np.linalg.norm(c_qr) <= 1e-9
     assert np.allclose(M, M.T) and np.linalg.eigvalsh(M).min() > 0      # E M positive definite
     assert 0.0 < res < 1.0
+
+
+def test_terms_map_real_fields_to_real_fields():
+    # A real operator has a symbol even in k (Sec. 3, remark on complex matrices):
+    # extending beta evenly from the half (real-FFT) grid to the full grid and
+    # applying it with a complex FFT must give a real field equal to the
+    # real-FFT evaluation -- also on even-length axes, where the Nyquist bin is
+    # its own negative wave vector.
+    for shape, pad in (((20, 26), 3), ((9, 14, 12), 2)):
+        h = (7.0,) * len(shape)
+        ang = [0, 2, -2, 4] if len(shape) == 2 else [0, 1, 2, 3, 4, 5]
+        b = Basis(shape, h, [(0,) * len(shape)], ang, 2, 0.08, order=-1.0, fft_pad=pad)
+        x = np.random.default_rng(4).standard_normal(shape)
+        nl = b.fshape[-1]
+        neg = [(-np.arange(N)) % N for N in b.fshape[:-1]]
+        for i in range(b.P):
+            _, a, q = b.index(i)
+            half = b.multiplier(a, q)
+            nh = half.shape[-1]
+            full = np.empty(b.fshape)
+            full[..., :nh] = half
+            for j in range(nh, nl):
+                full[..., j] = half[np.ix_(*neg, [(nl - j) % nl])][..., 0]
+            y = np.fft.ifftn(np.fft.fftn(b._pad(x)) * full)
+            assert np.abs(y.imag).max() <= 1e-12 * np.abs(y.real).max()
+            got = b.spatial_mode(0) * b._crop(y.real)
+            assert np.allclose(got, b.apply_term(i, x), atol=1e-12 * np.abs(got).max())
