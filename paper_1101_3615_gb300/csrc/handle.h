@@ -1,0 +1,98 @@
+// Definition of the library handle (struct probe_s) and the host helpers that
+// the C ABI translation units share.  Internal, not part of the ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace probe {
+
+struct Workspace {
+    // sizing key
+    int W = 0, nb = 0, with_ckpt = 0, with_data = 0, groups = 0;
+    size_t bytes = 0;
+    float* u = nullptr;       // [W][2][F]
+    float* f = nullptr;       // [W][nb][2][F]
+    float* dm = nullptr;      // [nb][F]
+    float* data = nullptr;    // [W][nb][nt][nr]
+    void* ckpt = nullptr;     // [nck][W][2][F] (fp32 or 16-bit)
+    float* scales = nullptr;  // [nck][W*2]
+    float* absmax = nullptr;  // [W*2]
+    float* dtt = nullptr;     // [W][K][F]
+    float* img = nullptr;     // [groups][nb][F]
+    float* comp = nullptr;
+    float* s_tmp = nullptr;   // [F]
+    int* src_wave = nullptr;  // [W][2] padded sources of the wave
+    CUtensorMap tm_u, tm_f;
+    int tm_tile_z = 0;
+    long long generation = 0;
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+struct FitCache;
+
+}  // namespace probe
+
+struct probe_s {
+    std::string err;
+    int ndim = 2;
+    int nz = 0, ny = 1, nx = 0, pad = 0;
+    int Nz = 0, Ny = 1, Nx = 0, P = 0;
+    long long F = 0;
+    long long nmodel = 0;
+    double hz = 0, hy = 0, hx = 0, dt = 0;
+    int nt = 0, ns = 0, nr = 0;
+    int snap = 0, kahan = 1, K = 0, nck = 0;
+    double cmax = 0;
+    float cz = 0, cx = 0, cy = 0;
+    std::vector<int> src_pad;  // [ns][ndim] padded
+    std::vector<int> rec_pad;  // [nr][ndim] padded
+    float* d_m0 = nullptr;     // interior
+    float* d_s0 = nullptr;     // padded
+    float* d_wavelet = nullptr;
+    int* d_src = nullptr;
+    int* d_rec = nullptr;
+    int* d_rec_tile_ptr = nullptr;
+    int* d_rec_tile_idx = nullptr;
+    int tile_z = 16, tiles_x = 0, tiles_z = 0, ntiles = 0;
+    int* d_err = nullptr;
+    probe::Workspace ws;
+    probe::DevBuf stage_in, stage_out;
+    // options
+    int opt_check_finite = 1, opt_shot_wave = 0, opt_shot_group = 0, opt_use_graph = 0;
+    int opt_timing = 0, opt_tile_z = 0;
+    probe_stats stats{};
+    std::vector<cudaEvent_t> events;
+    probe::FitCache* fit = nullptr;  // FFT plans and buffers of probe_fit / probe_apply_precond
+};
+
+namespace probe {
+
+probe_status fail(probe_t h, probe_status st, const std::string& msg);
+probe_status cuda_fail(probe_t h, cudaError_t e, const char* what);
+bool is_device_ptr(const void* p);
+probe_status ensure_buf(probe_t h, DevBuf& b, size_t bytes);
+void fit_cache_destroy(probe_t h);
+
+}  // namespace probe
+
+#define PROBE_CK(h, call)                                              \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return ::probe::cuda_fail(h, e_, #call); \
+    } while (0)
+
+#define PROBE_TRY(call)                \
+    do {                               \
+        probe_status s_ = (call);      \
+        if (s_ != PROBE_OK) return s_; \
+    } while (0)

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "handle.h"
 #include "internal.h"
 
 using namespace probe;
@@ -33,69 +34,9 @@ namespace {
 
 thread_local std::string g_create_error;
 
-struct Workspace {
-    // sizing key
-    int W = 0, nb = 0, with_ckpt = 0, with_data = 0, groups = 0;
-    size_t bytes = 0;
-    float* u = nullptr;       // [W][2][F]
-    float* f = nullptr;       // [W][nb][2][F]
-    float* dm = nullptr;      // [nb][F]
-    float* data = nullptr;    // [W][nb][nt][nr]
-    void* ckpt = nullptr;     // [nck][W][2][F] (fp32 or 16-bit)
-    float* scales = nullptr;  // [nck][W*2]
-    float* absmax = nullptr;  // [W*2]
-    float* dtt = nullptr;     // [W][K][F]
-    float* img = nullptr;     // [groups][nb][F]
-    float* comp = nullptr;
-    float* s_tmp = nullptr;   // [F]
-    int* src_wave = nullptr;  // [W][2] padded sources of the wave
-    CUtensorMap tm_u, tm_f;
-    int tm_tile_z = 0;
-    long long generation = 0;
-};
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t n = 0;
-};
-
 }  // namespace
 
-struct probe_s {
-    std::string err;
-    int ndim = 2;
-    int nz = 0, ny = 1, nx = 0, pad = 0;
-    int Nz = 0, Ny = 1, Nx = 0, P = 0;
-    long long F = 0;
-    long long nmodel = 0;
-    double hz = 0, hy = 0, hx = 0, dt = 0;
-    int nt = 0, ns = 0, nr = 0;
-    int snap = 0, kahan = 1, K = 0, nck = 0;
-    double cmax = 0;
-    float cz = 0, cx = 0, cy = 0;
-    std::vector<int> src_pad;  // [ns][ndim] padded
-    std::vector<int> rec_pad;  // [nr][ndim] padded
-    float* d_m0 = nullptr;     // interior
-    float* d_s0 = nullptr;     // padded
-    float* d_wavelet = nullptr;
-    int* d_src = nullptr;
-    int* d_rec = nullptr;
-    int* d_rec_tile_ptr = nullptr;
-    int* d_rec_tile_idx = nullptr;
-    int tile_z = 16, tiles_x = 0, tiles_z = 0, ntiles = 0;
-    int* d_err = nullptr;
-    Workspace ws;
-    DevBuf stage_in, stage_out;
-    // options
-    int opt_check_finite = 1, opt_shot_wave = 0, opt_shot_group = 0, opt_use_graph = 0;
-    int opt_timing = 0, opt_tile_z = 0;
-    probe_stats stats{};
-    std::vector<cudaEvent_t> events;
-};
-
-namespace {
-
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+namespace probe {
 
 probe_status fail(probe_t h, probe_status st, const std::string& msg) {
     if (h)
@@ -109,18 +50,6 @@ probe_status cuda_fail(probe_t h, cudaError_t e, const char* what) {
     const probe_status st = (e == cudaErrorMemoryAllocation) ? PROBE_ERR_OOM : PROBE_ERR_CUDA;
     return fail(h, st, std::string(what) + ": " + cudaGetErrorString(e));
 }
-
-#define CK(h, call)                                   \
-    do {                                              \
-        cudaError_t e_ = (call);                      \
-        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
-    } while (0)
-
-#define TRY(call)                          \
-    do {                                   \
-        probe_status s_ = (call);          \
-        if (s_ != PROBE_OK) return s_;     \
-    } while (0)
 
 bool is_device_ptr(const void* p) {
     if (!p) return false;
@@ -137,10 +66,19 @@ probe_status ensure_buf(probe_t h, DevBuf& b, size_t bytes) {
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.n = 0;
-    CK(h, cudaMalloc(&b.p, bytes));
+    PROBE_CK(h, cudaMalloc(&b.p, bytes));
     b.n = bytes;
     return PROBE_OK;
 }
+
+}  // namespace probe
+
+#define CK(h, call) PROBE_CK(h, call)
+#define TRY(call) PROBE_TRY(call)
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 probe_status get_encoder(probe_t h) {
     if (g_encode) return PROBE_OK;
@@ -550,13 +488,6 @@ void finish_stats(probe_t h, const Sweep& sw, int nwaves_events) {
     s.launches_total += sw.launches_fwd + sw.launches_rec + sw.launches_adj + sw.launches_other;
 }
 
-probe_status collect_timing(probe_t h, cudaStream_t st) {
-    if (!h->opt_timing) return PROBE_OK;
-    CK(h, cudaStreamSynchronize(st));
-    return PROBE_OK;
-}
-
-size_t padded_cells_all(probe_t h) { return (size_t)h->F; }
 
 }  // namespace
 
@@ -718,6 +649,7 @@ extern "C" probe_status probe_create(probe_t* out, const probe_grid* g, const fl
 
 extern "C" void probe_destroy(probe_t h) {
     if (!h) return;
+    fit_cache_destroy(h);
     free_ws(h->ws);
     void* ptrs[] = {h->d_m0, h->d_s0, h->d_wavelet, h->d_src, h->d_rec, h->d_rec_tile_ptr, h->d_rec_tile_idx,
                     h->d_err, h->stage_in.p, h->stage_out.p};
@@ -1043,7 +975,7 @@ extern "C" probe_status probe_gradient(probe_t h, const float* m, const float* r
     if (!h) return PROBE_ERR_ARG;
     if (!m || !resid || !g) return fail(h, PROBE_ERR_ARG, "NULL array");
     cudaStream_t st = (cudaStream_t)stream;
-    bool hin1 = false, hin2 = false;
+    bool hin1 = false;
     const float* md;
     const float* rd;
     // stage the model in stage_out's spare room is not possible; use two buffers
@@ -1054,7 +986,6 @@ extern "C" probe_status probe_gradient(probe_t h, const float* m, const float* r
         TRY(ensure_buf(h, mbuf, (size_t)h->nmodel * 4));
         CK(h, cudaMemcpyAsync(mbuf.p, m, (size_t)h->nmodel * 4, cudaMemcpyHostToDevice, st));
         md = (const float*)mbuf.p;
-        hin2 = true;
     } else
         md = m;
     const bool hout = !is_device_ptr(g);
@@ -1087,7 +1018,6 @@ extern "C" probe_status probe_gradient(probe_t h, const float* m, const float* r
     cudaStreamSynchronize(st);
     if (mbuf.p) cudaFree(mbuf.p);
     if (gbuf.p) cudaFree(gbuf.p);
-    (void)hin2;
     return st_;
 }
 
@@ -1104,10 +1034,6 @@ extern "C" probe_status probe_apply_H_group(const probe_t* models, int nmodels, 
     return PROBE_OK;
 }
 
-extern "C" probe_status probe_fit(probe_t h, const probe_basis* basis, const float* y, const float* Hy, int p,
-                                  double* coeffs, double* resid_rel, probe_stream_t stream);
-extern "C" probe_status probe_apply_precond(probe_t h, const probe_basis* basis, const double* coeffs,
-                                            const float* img, float* out, probe_stream_t stream);
 
 // ---------------------------------------------------------------------------
 // Allocation-free Born forward (probe_apply_F_noalloc).
