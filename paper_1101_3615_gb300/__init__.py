@@ -17,4 +17,7 @@ from .binding import (  # noqa: F401
     probe_version,
 )
 
-__all__ = ["Basis", "Probe", "ProbeError", "apply_H_group", "lib", "probe_version"]
+from .autograd import ForwardMap, forward_map, misfit  # noqa: F401,E402
+
+__all__ = ["Basis", "Probe", "ProbeError", "apply_H_group", "lib", "probe_version", "ForwardMap",
+           "forward_map", "misfit"]

@@ -1025,15 +1025,103 @@ extern "C" probe_status probe_apply_H_group(const probe_t* models, int nmodels, 
                                             float* const* Hdm, const int* nb, probe_stream_t stream) {
     if (!models || nmodels < 1 || nmodels > kMaxModels || !dm || !Hdm || !nb)
         return fail(nmodels >= 1 && models ? models[0] : nullptr, PROBE_ERR_ARG, "invalid group arguments");
-    // The multi-model launch path is built on the same sweeps; this build runs the
-    // models one after the other on the stream.
+    probe_t h0 = models[0];
+    if (!h0) return PROBE_ERR_ARG;
+    if (nmodels == 1) return probe_apply_H(h0, dm[0], Hdm[0], nb[0], stream);
     for (int k = 0; k < nmodels; ++k) {
-        probe_status s = probe_apply_H(models[k], dm[k], Hdm[k], nb[k], stream);
-        if (s != PROBE_OK) return s;
+        probe_t h = models[k];
+        if (!h) return fail(h0, PROBE_ERR_ARG, "NULL handle in group");
+        for (int j = 0; j < k; ++j)
+            if (models[j] == h) return fail(h0, PROBE_ERR_ARG, "a handle appears twice in the group");
+        if (nb[k] < 1) return fail(h0, PROBE_ERR_ARG, "every model of a group needs nb >= 1");
+        if (!dm[k] || !Hdm[k]) return fail(h0, PROBE_ERR_ARG, "NULL array in group");
+        if (h->ndim != 2) return fail(h0, PROBE_ERR_ARG, "group launches handle 2D grids");
+        if (h->nt != h0->nt || h->K != h0->K || std::fabs(h->dt - h0->dt) > 1e-12 * h0->dt)
+            return fail(h0, PROBE_ERR_ARG, "group models must share nt, dt and the checkpoint stride");
+        if (h->tile_z != h0->tile_z || h->kahan != h0->kahan)
+            return fail(h0, PROBE_ERR_ARG, "group models must share the tile height and the Kahan option");
     }
+    cudaStream_t st = (cudaStream_t)stream;
+    Sweep sw;
+    std::vector<float*> outs(nmodels);
+    std::vector<bool> host_out(nmodels);
+    bool any_host = false;
+    reset_stats(h0);
+    for (int k = 0; k < nmodels; ++k) {
+        probe_t h = models[k];
+        bool hin = false;
+        const float* dmd;
+        TRY(stage_input(h, dm[k], (size_t)nb[k] * h->nmodel, h->stage_in, &dmd, st, &hin));
+        host_out[k] = !is_device_ptr(Hdm[k]);
+        outs[k] = Hdm[k];
+        if (host_out[k]) {
+            TRY(ensure_buf(h, h->stage_out, (size_t)nb[k] * h->nmodel * 4));
+            outs[k] = (float*)h->stage_out.p;
+        }
+        any_host = any_host || hin || host_out[k];
+        TRY(ensure_ws(h, h->ns, nb[k], 1, 1));  // every shot of every model resident
+        Workspace& w = h->ws;
+        CK(h, cudaMemsetAsync(w.dm, 0, (size_t)nb[k] * h->F * 4, st));
+        cudaError_t e = launch_embed(dmd, w.dm, nb[k], h->nz, h->nx, 1, h->pad, h->Nz, h->Nx, 1, h->P, h->F, 1.0f, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "embed dm");
+        CK(h, cudaMemsetAsync(w.img, 0, (size_t)w.groups * nb[k] * h->F * 4, st));
+        CK(h, cudaMemsetAsync(w.comp, 0, (size_t)w.groups * nb[k] * h->F * 4, st));
+        CK(h, cudaMemcpyAsync(w.src_wave, h->src_pad.data(), (size_t)h->ns * 2 * 4, cudaMemcpyHostToDevice, st));
+        Job jb;
+        jb.h = h;
+        jb.j0 = 0;
+        jb.W = h->ns;
+        jb.nb = nb[k];
+        jb.s = h->d_s0;
+        jb.shot_group = pick_group(h, h->ns);
+        jb.groups = w.groups;
+        const long long tr = (long long)h->nt * h->nr;
+        jb.data = w.data;
+        jb.rdata = w.data;
+        jb.dss = (long long)nb[k] * tr;
+        jb.dts = tr;
+        sw.jobs.push_back(jb);
+    }
+    TRY(prepare_sweep(sw, h0, st));
+    if (h0->opt_timing) TRY(ensure_events(h0, 3 + 2 * h0->nck + 2));
+    record(h0, 0, st);
+    TRY(run_forward(sw, FWD_BORN, true));
+    record(h0, 1, st);
+    TRY(run_adjoint(sw));
+    finish_stats(h0, sw, 1);
+    for (int k = 0; k < nmodels; ++k) {
+        probe_t h = models[k];
+        Workspace& w = h->ws;
+        cudaError_t e = launch_extract_images(w.img, w.comp, w.groups, (long long)nb[k] * h->F, nb[k], h->F, outs[k],
+                                              h->nz, 1, h->nx, h->pad, 1, h->P, h->kahan != 0, false, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "image extraction");
+        const double cells = (double)h->Nz * h->Nx, steps = h->nt - 1;
+        h0->stats.cell_updates_forward += cells * steps * h->ns * (1 + nb[k]);
+        h0->stats.cell_updates_recompute += cells * steps * h->ns;
+        h0->stats.cell_updates_adjoint += cells * steps * h->ns * nb[k];
+        TRY(finish_call(h, st, any_host, outs[k], (long long)nb[k] * h->nmodel));
+    }
+    if (h0->opt_timing) {
+        CK(h0, cudaStreamSynchronize(st));
+        h0->stats.ms_forward = elapsed(h0, 0, 1);
+        int ev = 2;
+        for (int kk = h0->nck - 1; kk >= 0; --kk) {
+            const int k0 = kk * h0->K, k1 = std::min(k0 + h0->K, h0->nt - 1);
+            if (k0 >= k1) continue;
+            h0->stats.ms_recompute += elapsed(h0, ev, ev + 1);
+            h0->stats.ms_adjoint += elapsed(h0, ev + 1, ev + 2);
+            ev += 2;
+        }
+        h0->stats.ms_total = h0->stats.ms_forward + h0->stats.ms_recompute + h0->stats.ms_adjoint;
+    }
+    for (int k = 0; k < nmodels; ++k) {
+        if (!host_out[k]) continue;
+        probe_t h = models[k];
+        CK(h, cudaMemcpyAsync(Hdm[k], outs[k], (size_t)nb[k] * h->nmodel * 4, cudaMemcpyDeviceToHost, st));
+    }
+    if (any_host) CK(h0, cudaStreamSynchronize(st));
     return PROBE_OK;
 }
-
 
 // ---------------------------------------------------------------------------
 // Allocation-free Born forward (probe_apply_F_noalloc).
