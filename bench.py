@@ -201,6 +201,21 @@ def ncu_traffic(kind):
         return None
 
 
+def reduce_max(x, dist=None, group=None):
+    """Max of a host scalar over the ranks (CPU tensor on a gloo group; identity at N = 1)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank, world, ms_step_max):
+    """Whole-job throughput: units processed by all ranks / the slowest rank's step time."""
+    return units_per_rank * world / (ms_step_max * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 def main():
     a = parse()
@@ -266,16 +281,14 @@ def main():
         dist.barrier()
     from paper_1101_3615_gb300 import Probe
 
+    timing_group = dist.new_group(backend="gloo") if dist else None
+
     def barrier():
         if dist:
             dist.barrier()
 
     def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist, timing_group)
 
     p = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet, snapshot_dtype=a.snapshot)
     p.set_option("check_finite", 0)
@@ -316,8 +329,8 @@ def main():
     clocks = sampler.stop()
     ms_total = max_over_ranks(e0.elapsed_time(e1))
     ms_step = ms_total / a.steps
-    value = cells_per_h * world / (ms_step * 1e-3) / 1e9
-    h_per_s = wl.trials.shape[0] * world / (ms_step * 1e-3)
+    value = weak_scaling_value(cells_per_h, world, ms_step) / 1e9
+    h_per_s = weak_scaling_value(wl.trials.shape[0], world, ms_step)
     stats = p.stats()
     p.set_option("timing", 0)
 

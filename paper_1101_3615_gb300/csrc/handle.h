@@ -63,7 +63,7 @@ struct probe_s {
     int* d_rec = nullptr;
     int* d_rec_tile_ptr = nullptr;
     int* d_rec_tile_idx = nullptr;
-    int tile_z = 16, tiles_x = 0, tiles_z = 0, ntiles = 0;
+    int tile_z = 16, tiles_x = 0, tiles_y = 1, tiles_z = 0, ntiles = 0;
     int* d_err = nullptr;
     probe::Workspace ws;
     probe::DevBuf stage_in, stage_out;

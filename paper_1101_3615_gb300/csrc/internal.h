@@ -18,6 +18,8 @@ constexpr int kMaxModels = 4;
 constexpr int kTX = 64;        // 2D tile width (x), 16 float4 lanes
 constexpr int kThreads = 256;  // threads per stencil CTA
 constexpr int kMaxNbc = 8;     // trials per adjoint CTA (register accumulators)
+constexpr int kTY3D = 16;      // 3D tile height (y)
+constexpr int kZC3D = 32;      // 3D planes marched by one CTA
 
 // ---------------------------------------------------------------------------
 // Kernel parameter block of one model inside a (possibly multi-model) launch.
@@ -29,7 +31,8 @@ struct alignas(128) ModelStep2D {
     CUtensorMap tm_f;  // Born / adjoint planes  [W*nb*2][Nz][P]
     int Nz, Nx, P, pad, nz, nx;
     int tiles_x, tiles_z, ntiles;
-    int block_begin;   // first linear block index of this model in the launch
+    int block_begin;   // first grid.z index of this model in the launch
+    int chunk;         // adjoint: trial chunk of this launch
     int nshots;        // shots resident in this launch
     int nb;            // trials (Born / adjoint fields per shot)
     int shot_group;    // adjoint: shots handled by one CTA
@@ -40,6 +43,7 @@ struct alignas(128) ModelStep2D {
     float cz, cx;      // sponge: eta dt/2 = cz rho_z^2 + cx rho_x^2
     float c0;          // w0 (1/hz^2 + 1/hx^2)
     float lz[4], lx[4];  // w_k / h^2 per axis, k = 1..4
+    float cxm[4];        // x taps in first-difference form: sum_{k>m} w_k / hx^2, m = 0..3
     float inv_dt2;
     float vol_inv;     // 1 / (hz hx)
     long long F;       // floats per plane (Nz * P)
@@ -70,7 +74,52 @@ struct StepParams2D {
     ModelStep2D m[kMaxModels];
 };
 
-// Launchers (stencil2d.cu).  `blocks` = total blocks over the models.
+// ---------------------------------------------------------------------------
+// 3D: one field kind per launch; grid = (tiles_x * tiles_y * zchunks, nshots * nfield).
+// ---------------------------------------------------------------------------
+enum Step3Mode { STEP3_INC = 0, STEP3_INC_SAMPLE = 1, STEP3_BORN = 2, STEP3_ADJ = 3 };
+
+struct alignas(128) ModelStep3D {
+    CUtensorMap tm;    // 4D map (x, y, z, volume) over the state being differentiated
+    int Nz, Ny, Nx, P, pad, nz, ny, nx;
+    int tiles_x, tiles_y, zchunks, ZC;
+    int nshots, nfield;  // fields per shot in this launch (1 incident, nb Born / adjoint)
+    int nvol_shot;       // volumes per shot in the state buffer (2 * nfield)
+    int nr;
+    float cz, cy, cx;
+    float lz[4], ly[4], lx[4];
+    float inv_dt2, vol_inv;
+    long long F;         // floats per volume (Nz * Ny * P)
+    float* state;
+    const float* s;
+    const float* dm;           // Born: [nb][F]
+    const float* Din;          // Born: Dtt u^n of each shot; adjoint: Dtt u^{n-1}
+    long long Din_shot_stride;
+    float* Dout;               // incident: where Dtt u^n goes (may be null)
+    long long Dout_shot_stride;
+    const float* wavelet;
+    const int* src;            // [W][3] padded (z, y, x)
+    const int* rec_ptr;        // CSR over (tile_y * tiles_x + tile_x) * Nz + z
+    const int* rec_idx;
+    const int* rec_zyx;        // [nr][3] padded
+    float* data;
+    const float* rdata;
+    long long dss, dts;
+    float* img;                // adjoint: [W][nb][F]
+    float* comp;
+};
+
+struct StepParams3D {
+    int n, nt;
+    int* err;
+    ModelStep3D m;
+};
+
+cudaError_t launch_step3d(int mode, bool kahan, const StepParams3D& p, cudaStream_t st);
+size_t step3d_smem_bytes();
+
+// Launchers (stencil2d.cu).  `zblocks` = grid.z extent: shots (forward) or shot
+// groups (adjoint) summed over the models of the launch.
 enum FwdKind { FWD_INCIDENT = 0, FWD_INCIDENT_DTT = 1, FWD_BORN = 2, FWD_INCIDENT_SAMPLE = 3 };
 cudaError_t launch_fwd2d(FwdKind kind, int tile_z, const StepParams2D& p, int blocks,
                          cudaStream_t st);

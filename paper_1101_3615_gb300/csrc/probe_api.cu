@@ -95,13 +95,24 @@ probe_status get_encoder(probe_t h) {
 // (64 + 8) x (tile_z + 8) box; out-of-range elements read as zero.
 probe_status encode_planes(probe_t h, CUtensorMap* map, float* base, int planes, int tile_z) {
     TRY(get_encoder(h));
-    cuuint64_t dims[3] = {(cuuint64_t)h->Nx, (cuuint64_t)h->Nz, (cuuint64_t)planes};
-    cuuint64_t strides[2] = {(cuuint64_t)h->P * 4, (cuuint64_t)h->F * 4};
-    cuuint32_t box[3] = {(cuuint32_t)(kTX + 8), (cuuint32_t)(tile_z + 8), 1};
-    cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r;
+    if (h->ndim == 2) {
+        cuuint64_t dims[3] = {(cuuint64_t)h->Nx, (cuuint64_t)h->Nz, (cuuint64_t)planes};
+        cuuint64_t strides[2] = {(cuuint64_t)h->P * 4, (cuuint64_t)h->F * 4};
+        cuuint32_t box[3] = {(cuuint32_t)(kTX + 8), (cuuint32_t)(tile_z + 8), 1};
+        r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        // (x, y, z, volume) with a one-plane (64 + 8) x (16 + 8) box
+        cuuint64_t dims[4] = {(cuuint64_t)h->Nx, (cuuint64_t)h->Ny, (cuuint64_t)h->Nz, (cuuint64_t)planes};
+        cuuint64_t strides[3] = {(cuuint64_t)h->P * 4, (cuuint64_t)h->Ny * h->P * 4, (cuuint64_t)h->F * 4};
+        cuuint32_t box[4] = {(cuuint32_t)(kTX + 8), (cuuint32_t)(kTY3D + 8), 1, 1};
+        r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     if (r != CUDA_SUCCESS)
         return fail(h, PROBE_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
     return PROBE_OK;
@@ -125,6 +136,7 @@ void ws_bytes(probe_t h, int nb, int with_ckpt, int with_data, double* per_shot,
     double ps = 2 * F4 + 2.0 * nb * F4;
     if (with_ckpt) ps += (double)h->nck * 2 * h->F * snap_bytes(h->snap) + (double)h->K * F4 + 16.0 * h->nck;
     if (with_data) ps += (double)nb * h->nt * h->nr * 4.0;
+    if (h->ndim == 3 && with_ckpt) ps += 2.0 * nb * F4;  // per-shot images + compensation
     *per_shot = ps;
     *fixed = nb * F4 + 2.0 * F4 * nb + F4;  // dm, one image group, s_tmp
 }
@@ -141,6 +153,7 @@ int plan_wave(probe_t h, int nb, int with_ckpt, int with_data) {
 }
 
 int pick_group(probe_t h, int W) {
+    if (h->ndim == 3) return 1;  // 3D kernels accumulate one image per shot and trial
     if (h->opt_shot_group > 0) return std::min(h->opt_shot_group, W);
     return std::min(4, W);
 }
@@ -172,6 +185,8 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
         TRY(alloc((void**)&w.scales, (size_t)h->nck * W * 2 * 4));
         TRY(alloc((void**)&w.absmax, (size_t)W * 2 * 4));
         TRY(alloc((void**)&w.dtt, (size_t)W * h->K * F * 4));
+    } else if (h->ndim == 3) {
+        TRY(alloc((void**)&w.dtt, (size_t)W * F * 4));  // Dtt u^n of the current step (Born source)
     }
     TRY(alloc((void**)&w.img, (size_t)G * std::max(nb, 1) * F * 4));
     TRY(alloc((void**)&w.comp, (size_t)G * std::max(nb, 1) * F * 4));
@@ -180,7 +195,7 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     // field planes must read as zero outside what the kernels write
     CK(h, cudaMemset(w.u, 0, (size_t)W * 2 * F * 4));
     CK(h, cudaMemset(w.f, 0, (size_t)W * std::max(nb, 1) * 2 * F * 4));
-    if (with_ckpt) CK(h, cudaMemset(w.dtt, 0, (size_t)W * h->K * F * 4));
+    if (w.dtt) CK(h, cudaMemset(w.dtt, 0, (size_t)W * (with_ckpt ? h->K : 1) * F * 4));
     w.W = W;
     w.nb = nb;
     w.with_ckpt = with_ckpt;
@@ -194,19 +209,33 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
 
 // Receivers grouped by 2D tile (CSR) for the in-tile sampling and injection.
 probe_status build_rec_tiles(probe_t h) {
-    h->tiles_x = (h->Nx + kTX - 1) / kTX;
-    h->tiles_z = (h->Nz + h->tile_z - 1) / h->tile_z;
-    h->ntiles = h->tiles_x * h->tiles_z;
-    std::vector<int> cnt(h->ntiles + 1, 0), idx(h->nr);
-    std::vector<int> tile_of(h->nr);
-    for (int r = 0; r < h->nr; ++r) {
-        const int z = h->rec_pad[2 * r], x = h->rec_pad[2 * r + 1];
-        tile_of[r] = (z / h->tile_z) * h->tiles_x + x / kTX;
-        cnt[tile_of[r] + 1]++;
+    std::vector<int> key(h->nr);
+    int nkeys;
+    if (h->ndim == 2) {
+        h->tiles_x = (h->Nx + kTX - 1) / kTX;
+        h->tiles_z = (h->Nz + h->tile_z - 1) / h->tile_z;
+        h->ntiles = h->tiles_x * h->tiles_z;
+        nkeys = h->ntiles;
+        for (int r = 0; r < h->nr; ++r) {
+            const int z = h->rec_pad[2 * r], x = h->rec_pad[2 * r + 1];
+            key[r] = (z / h->tile_z) * h->tiles_x + x / kTX;
+        }
+    } else {
+        h->tiles_x = (h->Nx + kTX - 1) / kTX;
+        h->tiles_y = (h->Ny + kTY3D - 1) / kTY3D;
+        h->tiles_z = (h->Nz + kZC3D - 1) / kZC3D;
+        h->ntiles = h->tiles_x * h->tiles_y * h->tiles_z;
+        nkeys = h->tiles_x * h->tiles_y * h->Nz;
+        for (int r = 0; r < h->nr; ++r) {
+            const int z = h->rec_pad[3 * r], y = h->rec_pad[3 * r + 1], x = h->rec_pad[3 * r + 2];
+            key[r] = ((y / kTY3D) * h->tiles_x + x / kTX) * h->Nz + z;
+        }
     }
-    for (int t = 0; t < h->ntiles; ++t) cnt[t + 1] += cnt[t];
+    std::vector<int> cnt(nkeys + 1, 0), idx(h->nr);
+    for (int r = 0; r < h->nr; ++r) cnt[key[r] + 1]++;
+    for (int t = 0; t < nkeys; ++t) cnt[t + 1] += cnt[t];
     std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-    for (int r = 0; r < h->nr; ++r) idx[pos[tile_of[r]]++] = r;
+    for (int r = 0; r < h->nr; ++r) idx[pos[key[r]]++] = r;
     if (h->d_rec_tile_ptr) cudaFree(h->d_rec_tile_ptr);
     if (h->d_rec_tile_idx) cudaFree(h->d_rec_tile_idx);
     h->d_rec_tile_ptr = h->d_rec_tile_idx = nullptr;
@@ -268,6 +297,11 @@ void fill_model(const Job& jb, ModelStep2D& m, int* blocks_fwd, int* blocks_adj)
         m.lz[k] = (float)(wk[k] / (h->hz * h->hz));
         m.lx[k] = (float)(wk[k] / (h->hx * h->hx));
     }
+    for (int mm = 0; mm < 4; ++mm) {
+        double cm = 0.0;
+        for (int k = mm; k < 4; ++k) cm += wk[k];
+        m.cxm[mm] = (float)(cm / (h->hx * h->hx));
+    }
     m.inv_dt2 = (float)(1.0 / (h->dt * h->dt));
     m.vol_inv = (float)(1.0 / (h->hz * h->hx));
     m.F = h->F;
@@ -289,8 +323,8 @@ void fill_model(const Job& jb, ModelStep2D& m, int* blocks_fwd, int* blocks_adj)
     m.img = w.img;
     m.comp = w.comp;
     m.img_group_stride = (long long)std::max(w.nb, 1) * h->F;
-    *blocks_fwd = jb.W * h->ntiles;
-    *blocks_adj = jb.groups * h->ntiles;
+    *blocks_fwd = jb.W;        // grid.z extent of the forward launches
+    *blocks_adj = jb.groups;   // grid.z extent of the adjoint launches
 }
 
 struct Sweep {
@@ -343,7 +377,7 @@ void set_grid(Sweep& sw, bool adjoint) {
     for (size_t k = 0; k < sw.jobs.size(); ++k) {
         sw.p.m[k].block_begin = b;
         const Job& jb = sw.jobs[k];
-        b += (adjoint ? jb.groups : jb.W) * jb.h->ntiles;
+        b += adjoint ? jb.groups : jb.W;
     }
 }
 
@@ -439,10 +473,175 @@ probe_status run_adjoint(Sweep& sw) {
         record(h0, ev++, sw.st);
         for (int n = k1; n >= k0 + 1; --n) {
             TRY(launch_adj_step(sw, n, n - 1 - k0));
-            sw.launches_adj++;
+            sw.launches_adj += sw.chunks;
         }
     }
     record(h0, ev++, sw.st);
+    return PROBE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// 3D sweeps: one launch per field kind and step (incident, Born trials, adjoint).
+// ---------------------------------------------------------------------------
+long long dtt_stride3(probe_t h) { return (long long)(h->ws.with_ckpt ? h->K : 1) * h->F; }
+
+void fill3d(const Job& jb, ModelStep3D& m) {
+    probe_t h = jb.h;
+    Workspace& w = h->ws;
+    memset(&m, 0, sizeof(m));
+    m.Nz = h->Nz;
+    m.Ny = h->Ny;
+    m.Nx = h->Nx;
+    m.P = h->P;
+    m.pad = h->pad;
+    m.nz = h->nz;
+    m.ny = h->ny;
+    m.nx = h->nx;
+    m.tiles_x = h->tiles_x;
+    m.tiles_y = h->tiles_y;
+    m.zchunks = h->tiles_z;
+    m.ZC = kZC3D;
+    m.nshots = jb.W;
+    m.nr = h->nr;
+    m.cz = h->cz;
+    m.cy = h->cy;
+    m.cx = h->cx;
+    const double wk[4] = {PROBE_W1, PROBE_W2, PROBE_W3, PROBE_W4};
+    for (int k = 0; k < 4; ++k) {
+        m.lz[k] = (float)(wk[k] / (h->hz * h->hz));
+        m.ly[k] = (float)(wk[k] / (h->hy * h->hy));
+        m.lx[k] = (float)(wk[k] / (h->hx * h->hx));
+    }
+    m.inv_dt2 = (float)(1.0 / (h->dt * h->dt));
+    m.vol_inv = (float)(1.0 / (h->hz * h->hy * h->hx));
+    m.F = h->F;
+    m.s = jb.s;
+    m.dm = w.dm;
+    m.wavelet = h->d_wavelet;
+    m.src = w.src_wave;
+    m.rec_ptr = h->d_rec_tile_ptr;
+    m.rec_idx = h->d_rec_tile_idx;
+    m.rec_zyx = h->d_rec;
+    m.data = jb.data;
+    m.rdata = jb.rdata;
+    m.dss = jb.dss;
+    m.dts = jb.dts;
+    m.img = w.img;
+    m.comp = w.comp;
+}
+
+struct Count3 {
+    long long fwd = 0, rec = 0, adj = 0, other = 0;
+};
+
+probe_status launch3(probe_t h, int mode, StepParams3D& p, int n, cudaStream_t st, const char* what) {
+    p.n = n;
+    cudaError_t e = launch_step3d(mode, h->kahan != 0, p, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    return PROBE_OK;
+}
+
+probe_status run_forward3d(const Job& jb, FwdKind kind, bool ckpt, cudaStream_t st, Count3& c) {
+    probe_t h = jb.h;
+    Workspace& w = h->ws;
+    const bool born = kind == FWD_BORN;
+    CK(h, cudaMemsetAsync(w.u, 0, (size_t)jb.W * 2 * h->F * 4, st));
+    if (born) CK(h, cudaMemsetAsync(w.f, 0, (size_t)jb.W * jb.nb * 2 * h->F * 4, st));
+    StepParams3D pi, pb;
+    fill3d(jb, pi.m);
+    pi.nt = h->nt;
+    pi.err = h->d_err;
+    pi.m.tm = w.tm_u;
+    pi.m.state = w.u;
+    pi.m.nfield = 1;
+    pi.m.nvol_shot = 2;
+    pi.m.Dout = born ? w.dtt : nullptr;
+    pi.m.Dout_shot_stride = dtt_stride3(h);
+    if (born) {
+        fill3d(jb, pb.m);
+        pb.nt = h->nt;
+        pb.err = h->d_err;
+        pb.m.tm = w.tm_f;
+        pb.m.state = w.f;
+        pb.m.nfield = jb.nb;
+        pb.m.nvol_shot = 2 * jb.nb;
+        pb.m.Din = w.dtt;
+        pb.m.Din_shot_stride = dtt_stride3(h);
+    }
+    const int imode = (kind == FWD_INCIDENT_SAMPLE) ? STEP3_INC_SAMPLE : STEP3_INC;
+    for (int n = 0; n < h->nt - 1; ++n) {
+        if (ckpt && n % h->K == 0) {
+            const int k = n / h->K;
+            const size_t per = (size_t)jb.W * 2 * h->F;
+            void* dst = (char*)w.ckpt + (size_t)k * per * snap_bytes(h->snap);
+            cudaError_t e = launch_encode_ckpt(w.u, jb.W * 2, h->F, n & 1, dst, w.scales + (size_t)k * jb.W * 2,
+                                               h->snap, w.absmax, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint store");
+            c.other += (h->snap == PROBE_SNAP_FP32) ? 0 : 2;
+        }
+        TRY(launch3(h, imode, pi, n, st, "incident step launch"));
+        c.fwd++;
+        if (born) {
+            TRY(launch3(h, STEP3_BORN, pb, n, st, "Born step launch"));
+            c.fwd++;
+        }
+    }
+    if (born || kind == FWD_INCIDENT_SAMPLE) {
+        cudaError_t e = launch_sample(born ? w.f : w.u, (long long)(born ? jb.nb : 1) * 2 * h->F, 2 * h->F,
+                                      (h->nt - 1) & 1, h->F, jb.W, born ? jb.nb : 1, h->d_rec, h->nr, h->P, 3,
+                                      h->Ny, jb.data, jb.dss, jb.dts, h->nt - 1, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "receiver sampling");
+        c.other++;
+    }
+    return PROBE_OK;
+}
+
+probe_status run_adjoint3d(const Job& jb, cudaStream_t st, Count3& c) {
+    probe_t h = jb.h;
+    Workspace& w = h->ws;
+    CK(h, cudaMemsetAsync(w.f, 0, (size_t)jb.W * jb.nb * 2 * h->F * 4, st));
+    StepParams3D pi, pa;
+    fill3d(jb, pi.m);
+    pi.nt = h->nt;
+    pi.err = h->d_err;
+    pi.m.tm = w.tm_u;
+    pi.m.state = w.u;
+    pi.m.nfield = 1;
+    pi.m.nvol_shot = 2;
+    pi.m.Dout_shot_stride = dtt_stride3(h);
+    fill3d(jb, pa.m);
+    pa.nt = h->nt;
+    pa.err = h->d_err;
+    pa.m.tm = w.tm_f;
+    pa.m.state = w.f;
+    pa.m.nfield = jb.nb;
+    pa.m.nvol_shot = 2 * jb.nb;
+    pa.m.Din_shot_stride = dtt_stride3(h);
+    int ev = 2;
+    for (int k = h->nck - 1; k >= 0; --k) {
+        const int k0 = k * h->K;
+        const int k1 = std::min(k0 + h->K, h->nt - 1);
+        if (k0 >= k1) continue;
+        record(h, ev++, st);
+        const size_t per = (size_t)jb.W * 2 * h->F;
+        const void* src = (const char*)w.ckpt + (size_t)k * per * snap_bytes(h->snap);
+        cudaError_t e = launch_decode_ckpt(src, w.scales + (size_t)k * jb.W * 2, jb.W * 2, h->F, k0 & 1, h->snap, w.u,
+                                           st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint restore");
+        c.other += (h->snap == PROBE_SNAP_FP32) ? 0 : 1;
+        for (int j = k0; j < k1; ++j) {
+            pi.m.Dout = w.dtt + (long long)(j - k0) * h->F;
+            TRY(launch3(h, STEP3_INC, pi, j, st, "recompute step launch"));
+            c.rec++;
+        }
+        record(h, ev++, st);
+        for (int n = k1; n >= k0 + 1; --n) {
+            pa.m.Din = w.dtt + (long long)(n - 1 - k0) * h->F;
+            TRY(launch3(h, STEP3_ADJ, pa, n, st, "adjoint step launch"));
+            c.adj++;
+        }
+    }
+    record(h, ev++, st);
     return PROBE_OK;
 }
 
@@ -502,7 +701,6 @@ extern "C" probe_status probe_create(probe_t* out, const probe_grid* g, const fl
     if (!g || !m0 || !src_idx || !rec_idx || !wavelet)
         return fail(nullptr, PROBE_ERR_ARG, "NULL argument");
     if (g->ndim != 2 && g->ndim != 3) return fail(nullptr, PROBE_ERR_ARG, "ndim must be 2 or 3");
-    if (g->ndim == 3) return fail(nullptr, PROBE_ERR_ARG, "3D grids are not supported by this build");
     for (int a = 0; a < g->ndim; ++a) {
         if (g->n[a] < 1 || g->n[a] > (1 << 20)) return fail(nullptr, PROBE_ERR_ARG, "grid size out of range");
         if (!(g->h[a] > 0) || !std::isfinite(g->h[a])) return fail(nullptr, PROBE_ERR_ARG, "spacing must be > 0");
@@ -515,20 +713,21 @@ extern "C" probe_status probe_create(probe_t* out, const probe_grid* g, const fl
     if (!(dt > 0) || !std::isfinite(dt)) return fail(nullptr, PROBE_ERR_ARG, "dt must be > 0");
 
     probe_t h = new probe_s();
-    h->ndim = g->ndim;
+    const int D = g->ndim;
+    h->ndim = D;
     h->nz = g->n[0];
-    h->nx = g->n[1];
-    h->ny = 1;
+    h->ny = D == 3 ? g->n[1] : 1;
+    h->nx = g->n[D - 1];
     h->hz = g->h[0];
-    h->hx = g->h[1];
-    h->hy = 1.0;
+    h->hy = D == 3 ? g->h[1] : 1.0;
+    h->hx = g->h[D - 1];
     h->pad = g->pad;
     h->Nz = h->nz + 2 * h->pad;
+    h->Ny = D == 3 ? h->ny + 2 * h->pad : 1;
     h->Nx = h->nx + 2 * h->pad;
-    h->Ny = 1;
     h->P = ((h->Nx + 31) / 32) * 32;
-    h->F = (long long)h->Nz * h->P;
-    h->nmodel = (long long)h->nz * h->nx;
+    h->F = (long long)h->Nz * h->Ny * h->P;
+    h->nmodel = (long long)h->nz * h->ny * h->nx;
     h->dt = dt;
     h->nt = nt;
     h->ns = ns;
@@ -543,10 +742,10 @@ extern "C" probe_status probe_create(probe_t* out, const probe_grid* g, const fl
         probe_destroy(h);
         return fail(nullptr, PROBE_ERR_ARG, m);
     };
-    // indices
-    h->src_pad.resize((size_t)ns * 2);
-    h->rec_pad.resize((size_t)nr * 2);
-    std::vector<int> sidx((size_t)ns * 2), ridx((size_t)nr * 2);
+    // indices (padded copies kept in the same (z[, y], x) order)
+    h->src_pad.resize((size_t)ns * D);
+    h->rec_pad.resize((size_t)nr * D);
+    std::vector<int> sidx((size_t)ns * D), ridx((size_t)nr * D);
     if (is_device_ptr(src_idx)) {
         if (cudaMemcpy(sidx.data(), src_idx, sidx.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
             return bad("cannot read src_idx");
@@ -557,18 +756,19 @@ extern "C" probe_status probe_create(probe_t* out, const probe_grid* g, const fl
             return bad("cannot read rec_idx");
     } else
         memcpy(ridx.data(), rec_idx, ridx.size() * 4);
-    for (int s = 0; s < ns; ++s) {
-        const int iz = sidx[2 * s], ix = sidx[2 * s + 1];
-        if (iz < 0 || iz >= h->nz || ix < 0 || ix >= h->nx) return bad("source index outside the interior");
-        h->src_pad[2 * s] = iz + h->pad;
-        h->src_pad[2 * s + 1] = ix + h->pad;
-    }
-    for (int r = 0; r < nr; ++r) {
-        const int iz = ridx[2 * r], ix = ridx[2 * r + 1];
-        if (iz < 0 || iz >= h->nz || ix < 0 || ix >= h->nx) return bad("receiver index outside the interior");
-        h->rec_pad[2 * r] = iz + h->pad;
-        h->rec_pad[2 * r + 1] = ix + h->pad;
-    }
+    const int nlim[3] = {h->nz, D == 3 ? h->ny : h->nx, h->nx};
+    for (int s = 0; s < ns; ++s)
+        for (int a = 0; a < D; ++a) {
+            const int v = sidx[(size_t)D * s + a];
+            if (v < 0 || v >= nlim[a]) return bad("source index outside the interior");
+            h->src_pad[(size_t)D * s + a] = v + h->pad;
+        }
+    for (int r = 0; r < nr; ++r)
+        for (int a = 0; a < D; ++a) {
+            const int v = ridx[(size_t)D * r + a];
+            if (v < 0 || v >= nlim[a]) return bad("receiver index outside the interior");
+            h->rec_pad[(size_t)D * r + a] = v + h->pad;
+        }
     // model: positivity, finiteness, CFL
     std::vector<float> m0h((size_t)h->nmodel);
     std::vector<float> wh((size_t)nt);
@@ -596,8 +796,9 @@ extern "C" probe_status probe_create(probe_t* out, const probe_grid* g, const fl
             return fail(nullptr, PROBE_ERR_NONFINITE, "wavelet must be finite");
         }
     h->cmax = 1.0 / std::sqrt((double)mmin);
-    const double hmin = std::min(h->hz, h->hx);
-    const double limit = 2.0 / std::sqrt(2.0 * (205.0 / 72.0 + 2 * (8.0 / 5 + 1.0 / 5 + 8.0 / 315 + 1.0 / 560)));
+    const double hmin = std::min(h->hz, std::min(h->hx, D == 3 ? h->hy : h->hx));
+    // leapfrog + 8th-order Laplacian: c dt / h < 2 / sqrt(D * (|w0| + 2 sum |w_k|))
+    const double limit = 2.0 / std::sqrt(D * (205.0 / 72.0 + 2 * (8.0 / 5 + 1.0 / 5 + 8.0 / 315 + 1.0 / 560)));
     if (h->cmax * dt / hmin >= limit) {
         char buf[160];
         snprintf(buf, sizeof buf, "CFL violated: c_max dt / h_min = %.4f >= %.4f", h->cmax * dt / hmin, limit);
@@ -606,10 +807,13 @@ extern "C" probe_status probe_create(probe_t* out, const probe_grid* g, const fl
     // sponge: eta dt/2 = (dt/2) eta_max (rho/pad)^2 per axis
     if (h->pad > 0) {
         const double R = 1e-3;
-        const double ez = 3.0 * h->cmax * std::log(1.0 / R) / (2.0 * h->pad * h->hz);
-        const double ex = 3.0 * h->cmax * std::log(1.0 / R) / (2.0 * h->pad * h->hx);
-        h->cz = (float)(0.5 * dt * ez / ((double)h->pad * h->pad));
-        h->cx = (float)(0.5 * dt * ex / ((double)h->pad * h->pad));
+        auto coef = [&](double ha) {
+            const double em = 3.0 * h->cmax * std::log(1.0 / R) / (2.0 * h->pad * ha);
+            return (float)(0.5 * dt * em / ((double)h->pad * h->pad));
+        };
+        h->cz = coef(h->hz);
+        h->cx = coef(h->hx);
+        h->cy = D == 3 ? coef(h->hy) : 0.f;
     }
 
     auto cuda_bad = [&](cudaError_t e, const char* what) {
@@ -622,7 +826,7 @@ extern "C" probe_status probe_create(probe_t* out, const probe_grid* g, const fl
     if ((e = cudaMemcpy(h->d_m0, m0h.data(), m0h.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_bad(e, "copy m0");
     if ((e = cudaMalloc(&h->d_s0, (size_t)h->F * 4)) != cudaSuccess) return cuda_bad(e, "alloc s0");
-    if ((e = launch_make_s(nullptr, h->d_m0, h->d_s0, h->nz, 1, h->nx, h->pad, h->P, h->F, h->Nz, 1, h->Nx,
+    if ((e = launch_make_s(nullptr, h->d_m0, h->d_s0, h->nz, h->ny, h->nx, h->pad, h->P, h->F, h->Nz, h->Ny, h->Nx,
                            (float)(dt * dt), 0)) != cudaSuccess)
         return cuda_bad(e, "make s0");
     if ((e = cudaMalloc(&h->d_wavelet, (size_t)nt * 4)) != cudaSuccess) return cuda_bad(e, "alloc wavelet");
@@ -744,8 +948,8 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
     h->stats.shot_group = pick_group(h, W);
     if (op == OP_F || op == OP_H) {
         CK(h, cudaMemsetAsync(w.dm, 0, (size_t)nb * h->F * 4, st));
-        cudaError_t e = launch_embed(dm_dev, w.dm, nb, h->nz, h->nx, 1, h->pad, h->Nz, h->Nx, 1, h->P, h->F,
-                                     1.0f, st);
+        cudaError_t e = launch_embed(dm_dev, w.dm, nb, h->nz, h->nx, h->ny, h->pad, h->Nz, h->Nx, h->Ny, h->P,
+                                     h->F, 1.0f, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "embed dm");
     }
     if (need_ckpt) {
@@ -759,8 +963,8 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
     for (int wv = 0; wv < nwaves; ++wv) {
         const int j0 = wv * W;
         const int Wv = std::min(W, h->ns - j0);
-        CK(h, cudaMemcpyAsync(w.src_wave, h->src_pad.data() + 2 * j0, (size_t)Wv * 2 * 4, cudaMemcpyHostToDevice,
-                              st));
+        CK(h, cudaMemcpyAsync(w.src_wave, h->src_pad.data() + (size_t)h->ndim * j0, (size_t)Wv * h->ndim * 4,
+                              cudaMemcpyHostToDevice, st));
         Sweep sw;
         Job jb;
         jb.h = h;
@@ -799,16 +1003,28 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
                 jb.dts = 0;
                 break;
         }
-        sw.jobs.push_back(jb);
-        TRY(prepare_sweep(sw, h, st));
-        record(h, 0, st);
         FwdKind kind = (op == OP_F || op == OP_H) ? FWD_BORN
                        : (op == OP_NONLIN)        ? FWD_INCIDENT_SAMPLE
                                                   : FWD_INCIDENT;
-        TRY(run_forward(sw, kind, need_ckpt));
-        record(h, 1, st);
-        if (need_ckpt) TRY(run_adjoint(sw));
-        finish_stats(h, sw, nwaves);
+        if (h->ndim == 3) {
+            Count3 c3;
+            record(h, 0, st);
+            TRY(run_forward3d(jb, kind, need_ckpt, st, c3));
+            record(h, 1, st);
+            if (need_ckpt) TRY(run_adjoint3d(jb, st, c3));
+            h->stats.launches_forward += c3.fwd;
+            h->stats.launches_recompute += c3.rec;
+            h->stats.launches_adjoint += c3.adj;
+            h->stats.launches_total += c3.fwd + c3.rec + c3.adj + c3.other;
+        } else {
+            sw.jobs.push_back(jb);
+            TRY(prepare_sweep(sw, h, st));
+            record(h, 0, st);
+            TRY(run_forward(sw, kind, need_ckpt));
+            record(h, 1, st);
+            if (need_ckpt) TRY(run_adjoint(sw));
+            finish_stats(h, sw, nwaves);
+        }
         const double cells = (double)h->Nz * h->Ny * h->Nx;
         const double steps = h->nt - 1;
         const int nfields = (kind == FWD_BORN) ? 1 + nbw : 1;
@@ -844,7 +1060,7 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
     }
     if (need_ckpt && img_out) {
         cudaError_t e = launch_extract_images(w.img, w.comp, G, (long long)nbw * h->F, nbw, h->F, img_out, h->nz,
-                                              1, h->nx, h->pad, 1, h->P, h->kahan != 0, false, st);
+                                              h->ny, h->nx, h->pad, h->Ny, h->P, h->kahan != 0, false, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "image extraction");
         h->stats.launches_total++;
     }
@@ -958,8 +1174,8 @@ extern "C" probe_status probe_forward_nonlinear(probe_t h, const float* m, float
     }
     TRY(ensure_ws(h, plan_wave(h, 1, 0, 0), 1, 0, 0));
     // positivity of m is the caller's responsibility; non-finite values are caught by the output check
-    cudaError_t e = launch_make_s(md, h->d_m0, h->ws.s_tmp, h->nz, 1, h->nx, h->pad, h->P, h->F, h->Nz, 1, h->Nx,
-                                  (float)(h->dt * h->dt), st);
+    cudaError_t e = launch_make_s(md, h->d_m0, h->ws.s_tmp, h->nz, h->ny, h->nx, h->pad, h->P, h->F, h->Nz, h->Ny,
+                                  h->Nx, (float)(h->dt * h->dt), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "make s");
     TRY(run_op(h, OP_NONLIN, nullptr, nullptr, dd, nullptr, 1, h->ws.s_tmp, st));
     TRY(finish_call(h, st, hin || hout, dd, (long long)nd));
@@ -999,8 +1215,8 @@ extern "C" probe_status probe_gradient(probe_t h, const float* m, const float* r
     do {
         st_ = ensure_ws(h, plan_wave(h, 1, 1, 0), 1, 1, 0);
         if (st_ != PROBE_OK) break;
-        cudaError_t e = launch_make_s(md, h->d_m0, h->ws.s_tmp, h->nz, 1, h->nx, h->pad, h->P, h->F, h->Nz, 1,
-                                      h->Nx, (float)(h->dt * h->dt), st);
+        cudaError_t e = launch_make_s(md, h->d_m0, h->ws.s_tmp, h->nz, h->ny, h->nx, h->pad, h->P, h->F, h->Nz,
+                                      h->Ny, h->Nx, (float)(h->dt * h->dt), st);
         if (e != cudaSuccess) {
             st_ = cuda_fail(h, e, "make s");
             break;
@@ -1239,6 +1455,11 @@ extern "C" probe_status probe_apply_F_noalloc(probe_t h, const float* dm, float*
         m.lz[k] = (float)(wk[k] / (h->hz * h->hz));
         m.lx[k] = (float)(wk[k] / (h->hx * h->hx));
     }
+    for (int mm = 0; mm < 4; ++mm) {
+        double cm = 0.0;
+        for (int k = mm; k < 4; ++k) cm += wk[k];
+        m.cxm[mm] = (float)(cm / (h->hx * h->hx));
+    }
     m.inv_dt2 = (float)(1.0 / (h->dt * h->dt));
     m.vol_inv = (float)(1.0 / (h->hz * h->hx));
     m.F = h->F;
@@ -1262,7 +1483,7 @@ extern "C" probe_status probe_apply_F_noalloc(probe_t h, const float* dm, float*
         m.data = d + (long long)j0 * tr;
         for (int n = 0; n < h->nt - 1; ++n) {
             p.n = n;
-            e = launch_fwd2d(FWD_BORN, h->tile_z, p, Wv * h->ntiles, st);
+            e = launch_fwd2d(FWD_BORN, h->tile_z, p, Wv, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "forward step launch");
         }
         e = launch_sample(s_f, (long long)nb * 2 * h->F, 2 * h->F, (h->nt - 1) & 1, h->F, Wv, nb, h->d_rec, h->nr,

@@ -31,20 +31,25 @@ struct Tile2D {
     static constexpr int ROWS = TZ / 16;
 };
 
-__device__ __forceinline__ int find_model(const StepParams2D& p, int blk) {
+// Grid: x = tile column, y = tile row, z = (model, shot or shot group) linearised
+// over the models of the launch; CTAs beyond a smaller model's tile range exit.
+__device__ __forceinline__ int find_model(const StepParams2D& p, int bz) {
     int mi = 0;
 #pragma unroll
     for (int k = 1; k < kMaxModels; ++k)
-        if (k < p.nmodels && blk >= p.m[k].block_begin) mi = k;
+        if (k < p.nmodels && bz >= p.m[k].block_begin) mi = k;
     return mi;
 }
 
 // Laplacian of the 4 cells starting at tile coordinates (row, col) (col % 4 == 0).
-// Each tap pair is accumulated as (u[+k] - u) + (u[-k] - u): since the weights
-// satisfy w0 = -2 sum_k w_k this equals w0 u + sum_k w_k (u[+k] + u[-k]), but the
-// differences of neighbouring values are nearly exact in FP32, which removes the
-// cancellation between the centre term and the neighbour sums (the dominant
-// round-off of the time stepping for smooth, well-sampled fields).
+// The taps are accumulated from differences of neighbouring values, never from
+// the raw values against the centre term: those differences are nearly exact in
+// FP32, which removes the cancellation that otherwise dominates the round-off
+// of the time stepping for smooth, well-sampled fields.
+//   x: with d_i = v_{i+1} - v_i,  sum_k w_k (v_{c+k} + v_{c-k} - 2 v_c)
+//        = sum_{m=0..3} C_m (d_{c+m} - d_{c-m-1}),  C_m = sum_{k>m} w_k
+//      (11 shared differences for the thread's 4 cells);
+//   z: (v_{+k} - v) + (v_{-k} - v) per tap pair.
 template <int HX>
 __device__ __forceinline__ void lap4(const float* t, int row, int col, const ModelStep2D& M,
                                      float4& center, float L[4]) {
@@ -52,12 +57,14 @@ __device__ __forceinline__ void lap4(const float* t, int row, int col, const Mod
     const float4 a = ld4(rp - 4), b = ld4(rp), c = ld4(rp + 4);
     const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
     center = b;
+    float d[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) d[i] = v[i + 1] - v[i];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float u0 = v[4 + j];
-        float acc = 0.f;
+        float acc = M.cxm[0] * (d[4 + j] - d[3 + j]);
 #pragma unroll
-        for (int k = 1; k <= 4; ++k) acc = fmaf(M.lx[k - 1], (v[4 + j + k] - u0) + (v[4 + j - k] - u0), acc);
+        for (int m = 1; m < 4; ++m) acc = fmaf(M.cxm[m], d[4 + j + m] - d[3 + j - m], acc);
         L[j] = acc;
     }
 #pragma unroll
@@ -112,13 +119,12 @@ __global__ void __launch_bounds__(kThreads) k_fwd2d(const __grid_constant__ Step
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bars[3];
 
-    const int mi = find_model(p, blockIdx.x);
+    const int mi = find_model(p, blockIdx.z);
     const ModelStep2D& M = p.m[mi];
-    const int blk = blockIdx.x - M.block_begin;
-    const int shot = blk / M.ntiles;
-    const int tile = blk - shot * M.ntiles;
-    const int tzi = tile / M.tiles_x;
-    const int z0 = tzi * TZ, x0 = (tile - tzi * M.tiles_x) * kTX;
+    if ((int)blockIdx.x >= M.tiles_x || (int)blockIdx.y >= M.tiles_z) return;
+    const int shot = blockIdx.z - M.block_begin;
+    const int tile = blockIdx.y * M.tiles_x + blockIdx.x;
+    const int z0 = blockIdx.y * TZ, x0 = blockIdx.x * kTX;
     const int tid = threadIdx.x;
     const int lx = (tid & 15) << 2, lz = tid >> 4;
     const int n = p.n;
@@ -145,6 +151,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd2d(const __grid_constant__ Step
     }
 
     const int x = x0 + lx;
+    const bool full = (x0 + kTX <= M.Nx);  // no pitch column inside this tile
     float* ubase = M.u + (long long)(shot * 2) * F;
     float4 sv[ROWS], uo[ROWS];
     long long off[ROWS];
@@ -179,19 +186,22 @@ __global__ void __launch_bounds__(kThreads) k_fwd2d(const __grid_constant__ Step
             if (j >= 0 && j < 4) L[j] += fsrc;
         }
         float o[4];
+        const bool interior = (z >= M.pad) && (z < M.pad + M.nz) && (x >= M.pad) && (x + 3 < M.pad + M.nx);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const float Fo = get(sv[r], j) * L[j];
             D[r][j] = Fo * M.inv_dt2;
-            const float e = sponge_e(M, z, x + j);
             float G = 1.f, am = 1.f;
-            if (e != 0.f) {
-                G = __frcp_rn(1.f + e);
-                am = 1.f - e;
+            if (!interior) {
+                const float e = sponge_e(M, z, x + j);
+                if (e != 0.f) {
+                    G = __frcp_rn(1.f + e);
+                    am = 1.f - e;
+                }
             }
             Gc[r][j] = G;
             Am[r][j] = am;
-            o[j] = (x + j < M.Nx) ? G * (2.f * get(c, j) - am * get(uo[r], j) + Fo) : 0.f;
+            o[j] = (full || x + j < M.Nx) ? G * (2.f * get(c, j) - am * get(uo[r], j) + Fo) : 0.f;
         }
         if (valid[r]) {
             st4(ubase + po * F + off[r], make_float4(o[0], o[1], o[2], o[3]));
@@ -237,9 +247,9 @@ __global__ void __launch_bounds__(kThreads) k_fwd2d(const __grid_constant__ Step
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const float src = L[j] - get(dv[r], j) * D[r][j];
-                    o[j] = (x + j < M.Nx) ? Gc[r][j] * (2.f * get(c, j) - Am[r][j] * get(fo[r], j) +
-                                                        get(sv[r], j) * src)
-                                          : 0.f;
+                    o[j] = (full || x + j < M.Nx) ? Gc[r][j] * (2.f * get(c, j) - Am[r][j] * get(fo[r], j) +
+                                                                get(sv[r], j) * src)
+                                                  : 0.f;
                 }
                 if (valid[r]) st4(fb + po * F + off[r], make_float4(o[0], o[1], o[2], o[3]));
             }
@@ -260,13 +270,12 @@ __global__ void __launch_bounds__(kThreads) k_adj2d(const __grid_constant__ Step
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bars[2];
 
-    const int mi = find_model(p, blockIdx.x);
+    const int mi = find_model(p, blockIdx.z);
     const ModelStep2D& M = p.m[mi];
-    const int blk = blockIdx.x - M.block_begin;
-    const int grp = blk / M.ntiles;
-    const int tile = blk - grp * M.ntiles;
-    const int tzi = tile / M.tiles_x;
-    const int z0 = tzi * TZ, x0 = (tile - tzi * M.tiles_x) * kTX;
+    if ((int)blockIdx.x >= M.tiles_x || (int)blockIdx.y >= M.tiles_z) return;
+    const int grp = blockIdx.z - M.block_begin;
+    const int tile = blockIdx.y * M.tiles_x + blockIdx.x;
+    const int z0 = blockIdx.y * TZ, x0 = blockIdx.x * kTX;
     const int tid = threadIdx.x;
     const int lx = (tid & 15) << 2, lz = tid >> 4;
     const int n = p.n;
@@ -274,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) k_adj2d(const __grid_constant__ Step
     const int po = n & 1;        // plane of mu^{n+2}, overwritten by mu^n
     const long long F = M.F;
     const int nb = M.nb;
-    const int b0 = blockIdx.y * NBC;
+    const int b0 = M.chunk * NBC;
     if (b0 >= nb) return;
     const int nbc = min(NBC, nb - b0);
     const int j0 = grp * M.shot_group;
@@ -298,6 +307,7 @@ __global__ void __launch_bounds__(kThreads) k_adj2d(const __grid_constant__ Step
     }
 
     const int x = x0 + lx;
+    const bool full = (x0 + kTX <= M.Nx);
     float4 sv[ROWS];
     long long off[ROWS];
     bool valid[ROWS];
@@ -308,14 +318,17 @@ __global__ void __launch_bounds__(kThreads) k_adj2d(const __grid_constant__ Step
         valid[r] = (z < M.Nz) && (x < M.Nx);
         off[r] = (long long)z * M.P + x;
         sv[r] = valid[r] ? ld4(M.s + off[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool interior = (z >= M.pad) && (z < M.pad + M.nz) && (x >= M.pad) && (x + 3 < M.pad + M.nx);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float e = sponge_e(M, z, x + j);
             Gc[r][j] = 1.f;
             Am[r][j] = 1.f;
-            if (e != 0.f) {
-                Gc[r][j] = __frcp_rn(1.f + e);
-                Am[r][j] = 1.f - e;
+            if (!interior) {
+                const float e = sponge_e(M, z, x + j);
+                if (e != 0.f) {
+                    Gc[r][j] = __frcp_rn(1.f + e);
+                    Am[r][j] = 1.f - e;
+                }
             }
         }
     }
@@ -385,9 +398,9 @@ __global__ void __launch_bounds__(kThreads) k_adj2d(const __grid_constant__ Step
                     float o[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        o[j] = (x + j < M.Nx) ? Gc[r][j] * (2.f * get(c, j) - Am[r][j] * get(mo[r], j) +
-                                                            get(sv[r], j) * L[j])
-                                              : 0.f;
+                        o[j] = (full || x + j < M.Nx) ? Gc[r][j] * (2.f * get(c, j) - Am[r][j] * get(mo[r], j) +
+                                                                    get(sv[r], j) * L[j])
+                                                      : 0.f;
                         acc[bi][r][j] = fmaf(-get(Dv[r], j), o[j], acc[bi][r][j]);
                     }
                     if (valid[r]) st4(fb + po * F + off[r], make_float4(o[0], o[1], o[2], o[3]));
@@ -444,36 +457,51 @@ size_t adj2d_smem_bytes(int tile_z) {
 }
 
 template <int TZ>
-static cudaError_t launch_fwd_tz(FwdKind kind, const StepParams2D& p, int blocks, cudaStream_t st) {
+static cudaError_t launch_fwd_tz(FwdKind kind, const StepParams2D& p, dim3 grid, cudaStream_t st) {
     const size_t sm = fwd2d_smem_bytes(kind, TZ);
     switch (kind) {
-        case FWD_INCIDENT: k_fwd2d<TZ, FWD_INCIDENT><<<blocks, kThreads, sm, st>>>(p); break;
-        case FWD_INCIDENT_DTT: k_fwd2d<TZ, FWD_INCIDENT_DTT><<<blocks, kThreads, sm, st>>>(p); break;
-        case FWD_BORN: k_fwd2d<TZ, FWD_BORN><<<blocks, kThreads, sm, st>>>(p); break;
+        case FWD_INCIDENT: k_fwd2d<TZ, FWD_INCIDENT><<<grid, kThreads, sm, st>>>(p); break;
+        case FWD_INCIDENT_DTT: k_fwd2d<TZ, FWD_INCIDENT_DTT><<<grid, kThreads, sm, st>>>(p); break;
+        case FWD_BORN: k_fwd2d<TZ, FWD_BORN><<<grid, kThreads, sm, st>>>(p); break;
         case FWD_INCIDENT_SAMPLE:
-            k_fwd2d<TZ, FWD_INCIDENT_SAMPLE><<<blocks, kThreads, sm, st>>>(p);
+            k_fwd2d<TZ, FWD_INCIDENT_SAMPLE><<<grid, kThreads, sm, st>>>(p);
             break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd2d(FwdKind kind, int tile_z, const StepParams2D& p, int blocks,
+static dim3 grid2d(const StepParams2D& p, int zblocks) {
+    int tx = 0, tz = 0;
+    for (int k = 0; k < p.nmodels; ++k) {
+        tx = max(tx, p.m[k].tiles_x);
+        tz = max(tz, p.m[k].tiles_z);
+    }
+    return dim3(tx, tz, zblocks);
+}
+
+cudaError_t launch_fwd2d(FwdKind kind, int tile_z, const StepParams2D& p, int zblocks,
                          cudaStream_t st) {
-    if (blocks <= 0) return cudaSuccess;
-    if (tile_z == 16) return launch_fwd_tz<16>(kind, p, blocks, st);
-    if (tile_z == 32) return launch_fwd_tz<32>(kind, p, blocks, st);
+    if (zblocks <= 0) return cudaSuccess;
+    const dim3 grid = grid2d(p, zblocks);
+    if (tile_z == 16) return launch_fwd_tz<16>(kind, p, grid, st);
+    if (tile_z == 32) return launch_fwd_tz<32>(kind, p, grid, st);
     return cudaErrorInvalidValue;
 }
 
 template <int TZ, int NBC>
-static cudaError_t launch_adj_nbc(bool kahan, const StepParams2D& p, int blocks, int chunks,
+static cudaError_t launch_adj_nbc(bool kahan, const StepParams2D& p, int zblocks, int chunks,
                                   cudaStream_t st) {
     const size_t sm = adj2d_smem_bytes(TZ);
-    dim3 grid(blocks, chunks);
-    if (kahan)
-        k_adj2d<TZ, NBC, true><<<grid, kThreads, sm, st>>>(p);
-    else
-        k_adj2d<TZ, NBC, false><<<grid, kThreads, sm, st>>>(p);
+    const dim3 grid = grid2d(p, zblocks);
+    // trial chunks run as separate launches of the same step (each writes its own trials)
+    StepParams2D q = p;
+    for (int c = 0; c < chunks; ++c) {
+        for (int k = 0; k < q.nmodels; ++k) q.m[k].chunk = c;
+        if (kahan)
+            k_adj2d<TZ, NBC, true><<<grid, kThreads, sm, st>>>(q);
+        else
+            k_adj2d<TZ, NBC, false><<<grid, kThreads, sm, st>>>(q);
+    }
     return cudaGetLastError();
 }
 
