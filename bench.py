@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-history", action="store_true",
+                    help="skip the extra measurement with the full Dtt history resident")
     ap.add_argument("--snapshot", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--profile", default=None, choices=["fwd", "adj"],
                     help="run only F (fwd) or F* (adj) once after one warm-up call: the small "
@@ -69,6 +71,7 @@ def profile_run(a, wl):
     p = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet, snapshot_dtype=a.snapshot)
     p.set_option("check_finite", 0)
     p.set_option("tile_z", 16)
+    p.set_option("use_graph", 1)      # each shot wave's sweeps replayed as one CUDA graph
     dm = torch.tensor(wl.trials, device=dev)
     if a.profile == "fwd":
         run = lambda: p.apply_F(dm)
@@ -181,20 +184,30 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    src = os.path.join(ROOT, "paper_1101_3615_gb300", "csrc", "stencil2d.cu")
+def kernel_source_hash(name):
+    src = os.path.join(ROOT, "paper_1101_3615_gb300", "csrc", name)
     with open(src, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def ncu_traffic(kind):
+def kernel_label(pipeline, adjoint):
+    """Kernel name and source file of the 2D forward / adjoint step variant the handle ran."""
+    if pipeline:
+        name = (f"k_adj2d_ws<nbc, kahan, S={pipeline}>" if adjoint else
+                f"k_fwd2d_ws<FWD_BORN, S={pipeline}> (fused incident + Born step, warp-specialised TMA ring)")
+        return name, "stencil2d_pipe.cu"
+    name = "k_adj2d<16, nbc, kahan>" if adjoint else "k_fwd2d<16, FWD_BORN> (fused incident + Born step)"
+    return name, "stencil2d.cu"
+
+
+def ncu_traffic(kind, source):
     """DRAM bytes per launch from the committed ncu summary, if it matches this kernel source."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d[kind]
-        if e.get("source_sha") != kernel_source_hash():
+        if e.get("source") != source or e.get("source_sha") != kernel_source_hash(source):
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:
@@ -258,7 +271,7 @@ def main():
     # CPU baseline first (spawned pool, before any CUDA work), rank 0 at N=1 only
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
-        nsh, nts = min(16, wl.ns, os.cpu_count() or 1), 101
+        nsh, nts = min(16, wl.ns, os.cpu_count() or 1), 251
         v, cores, wall = oracle_sample(a.config, nsh, nts)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{nsh} shots x {nts - 1} steps of H (F then F*) on the full "
@@ -293,6 +306,7 @@ def main():
     p = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet, snapshot_dtype=a.snapshot)
     p.set_option("check_finite", 0)
     p.set_option("tile_z", 16)
+    p.set_option("use_graph", 1)      # each shot wave's sweeps replayed as one CUDA graph
     dm = torch.tensor(wl.trials, device=dev)
     out = torch.empty_like(dm)
     stream = torch.cuda.current_stream(dev)
@@ -362,6 +376,35 @@ def main():
     dot_err = abs(lhs - rhs) / abs(lhs)
     del d, img
 
+    # same step with Dtt u^n of every time step kept in HBM (no checkpoint recompute)
+    hist = None
+    if not a.no_history:
+        ph = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet)
+        for k, v in (("check_finite", 0), ("tile_z", 16), ("use_graph", 1), ("dtt_history", 1)):
+            ph.set_option(k, v)
+        try:
+            for _ in range(2):
+                ph.apply_H(dm, out=out)
+            nh = max(2, min(a.steps, 4))
+            torch.cuda.synchronize(dev)
+            eh0 = torch.cuda.Event(enable_timing=True)
+            eh1 = torch.cuda.Event(enable_timing=True)
+            eh0.record(stream)
+            for _ in range(nh):
+                ph.apply_H(dm, out=out)
+            eh1.record(stream)
+            torch.cuda.synchronize(dev)
+            hms = max_over_ranks(eh0.elapsed_time(eh1) / nh)
+            hist = {"value": weak_scaling_value(cells_per_h, world, hms) / 1e9, "unit": UNIT,
+                    "h_applies_per_s": weak_scaling_value(wl.trials.shape[0], world, hms),
+                    "ms_per_h": hms, "steps": nh,
+                    "history_bytes": int(wl.ns * (wl.nt - 1) * wl.cells_padded() * 4),
+                    "how": "PROBE_OPT_DTT_HISTORY=1: FP32 Dtt u^n of all nt-1 steps resident, "
+                           "no recompute sweep; CUDA events, same inputs"}
+        except Exception as ex:  # not enough device memory for the history
+            hist = {"unavailable": str(ex).splitlines()[0][:200]}
+        del ph
+
     # plain per-shot FP32 path: one shot resident at a time, no shot grouping
     plain = None
     if not a.no_plain:
@@ -385,7 +428,9 @@ def main():
                  "how": f"one shot resident at a time, timed on {nsub} shots and scaled to {wl.ns}"}
         del pp
 
-    traffic = ncu_traffic("fwd_born")
+    fwd_name, fwd_src = kernel_label(stats["pipeline_forward"], False)
+    adj_name, adj_src = kernel_label(stats["pipeline_adjoint"], True)
+    traffic = ncu_traffic("fwd_born", fwd_src)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -395,7 +440,9 @@ def main():
                    "shots": wl.ns, "trials": int(wl.trials.shape[0]), "nt": wl.nt,
                    "snapshots": a.snapshot, "ckpt_stride": stats["ckpt_stride"],
                    "shot_wave": stats["shot_wave"], "shot_group": stats["shot_group"],
-                   "tile_z": stats["tile_z"],
+                   "tile_z": stats["tile_z"], "pipeline_forward": stats["pipeline_forward"],
+                   "pipeline_adjoint": stats["pipeline_adjoint"], "cuda_graph": True,
+                   "autotuned": True,
                    "l2": f"inputs larger than L2: {wl.ns} shots x 4 field planes x "
                          f"{wl.cells_padded() * 4 / 1e6:.2f} MB = "
                          f"{wl.ns * 4 * wl.cells_padded() * 4 / 1e6:.0f} MB live state per step "
@@ -404,11 +451,11 @@ def main():
         "h_applies_per_s": h_per_s,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_fwd2d<16, FWD_BORN> (fused incident + Born step)",
+                     "kernel": fwd_name,
                      "bytes_per_launch": fwd_launch_bytes, "avg_launch_ms": fwd_launch_ms,
                      "peak_kind": f"{peak_kind} hbm_gbs (copy)"},
         "adjoint_roofline": {"achieved": adj_achieved, "frac": adj_achieved / peak,
-                             "kernel": "k_adj2d<16,1,kahan> (adjoint step + imaging)"},
+                             "kernel": adj_name + " (adjoint step + imaging)"},
         "sweep_ms_per_step": {"forward": fwd_ms / a.steps, "recompute": rec_ms / a.steps,
                               "adjoint": adj_ms / a.steps},
         "e2e": e2e,
@@ -416,6 +463,7 @@ def main():
         "clocks": clocks,
         "plain": plain,
         "batched_over_plain": (value / plain["value"]) if plain else None,
+        "dtt_history": hist,
         "stated_error": {"fp32_dot_test": dot_err,
                          "hv_vs_oracle": "see tests/test_gpu_parity.py (1e-4 FP32, 2e-3 16-bit)"},
         "cpu_baseline": cpu,

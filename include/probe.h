@@ -110,7 +110,14 @@ typedef enum {
     PROBE_OPT_SHOT_GROUP = 3,    /* shots per CTA in the adjoint sweep; 0 = autotuned */
     PROBE_OPT_USE_GRAPH = 4,     /* 1 (default): replay sweeps from a captured CUDA graph */
     PROBE_OPT_TIMING = 5,        /* 1: record per-sweep CUDA-event timings (probe_get_stats) */
-    PROBE_OPT_TILE_Z = 6         /* 2D tile height override (8, 16 or 32); 0 = autotuned */
+    PROBE_OPT_TILE_Z = 6,        /* 2D tile height override (16 or 32); 0 = default */
+    PROBE_OPT_PIPELINE = 7,      /* 2D: 0 = one tile per CTA; 2, 3 or 4 = persistent warp-specialised
+                                    CTAs with a 2-, 3- or 4-stage TMA ring (tile height 16) */
+    PROBE_OPT_DTT_HISTORY = 8,   /* 2D: 1 = keep Dtt u^n of every step in device memory instead of
+                                    checkpointing and recomputing (FP32, W (nt-1) planes); 0 (default) */
+    PROBE_OPT_AUTOTUNE = 9       /* 1 (default): on the first call for a shape, time the kernel variants
+                                    (forward pipeline depth, adjoint variant and shot group) and keep the
+                                    fastest; setting PROBE_OPT_PIPELINE or PROBE_OPT_SHOT_GROUP turns it off */
 } probe_option;
 
 /* Counters and timings of the last apply call (probe_get_stats). */
@@ -133,6 +140,9 @@ typedef struct {
     int shot_group;              /* shots per CTA in the adjoint */
     int tile_z;                  /* 2D tile height used */
     int ckpt_stride;             /* checkpoint spacing used */
+    int pipeline_forward;        /* 2D forward kernel: 0 one tile per CTA, 2..4 pipeline stages */
+    int pipeline_adjoint;        /* 2D adjoint kernel: same encoding */
+    int dtt_history;             /* 1 when Dtt u^n of every step was kept instead of recomputed */
 } probe_stats;
 
 /* Create a handle for one background model and acquisition geometry.
@@ -218,6 +228,14 @@ probe_status probe_gradient(probe_t h, const float* m, const float* resid, float
  * allocating library routine is called. */
 probe_status probe_apply_F_noalloc(probe_t h, const float* dm, float* d, int nb,
                                    probe_stream_t stream);
+
+/* Failure-detection check (no counterpart in the paper): launches one CTA
+ * whose bounded mbarrier wait can never be satisfied, so it gives up after
+ * timeout_ms (1..10000) of device time, records the timeout in the handle's
+ * device error word and exits.  Returns PROBE_ERR_TIMEOUT (after synchronising
+ * `stream`); the handle and the CUDA context remain usable.  This is the same
+ * bounded-wait path every stencil kernel uses around its TMA loads. */
+probe_status probe_diag_wait_timeout(probe_t h, int timeout_ms, probe_stream_t stream);
 
 /* Set a tunable (probe_option); returns PROBE_ERR_ARG for unknown keys or values. */
 probe_status probe_set_option(probe_t h, int key, long long value);

@@ -20,7 +20,8 @@ PROBE_OK = 0
 STATUS = {0: "PROBE_OK", -1: "PROBE_ERR_ARG", -2: "PROBE_ERR_CUDA", -3: "PROBE_ERR_OOM",
           -4: "PROBE_ERR_TIMEOUT", -5: "PROBE_ERR_NONFINITE", -6: "PROBE_ERR_STATE"}
 SNAP = {"fp32": 0, "bf16": 1, "fp16": 2}
-OPT = {"check_finite": 1, "shot_wave": 2, "shot_group": 3, "use_graph": 4, "timing": 5, "tile_z": 6}
+OPT = {"check_finite": 1, "shot_wave": 2, "shot_group": 3, "use_graph": 4, "timing": 5, "tile_z": 6,
+       "pipeline": 7, "dtt_history": 8, "autotune": 9}
 
 
 class probe_grid(C.Structure):
@@ -43,7 +44,8 @@ class probe_stats(C.Structure):
                 ("cell_updates_adjoint", C.c_double), ("bytes_forward", C.c_double),
                 ("bytes_recompute", C.c_double), ("bytes_adjoint", C.c_double),
                 ("shot_wave", C.c_int), ("shot_group", C.c_int), ("tile_z", C.c_int),
-                ("ckpt_stride", C.c_int)]
+                ("ckpt_stride", C.c_int), ("pipeline_forward", C.c_int),
+                ("pipeline_adjoint", C.c_int), ("dtt_history", C.c_int)]
 
 
 class ProbeError(RuntimeError):
@@ -69,6 +71,7 @@ def _load():
         "probe_forward_nonlinear": (I, [P, VP, VP, VP]),
         "probe_gradient": (I, [P, VP, VP, VP, VP]),
         "probe_set_option": (I, [P, I, C.c_longlong]),
+        "probe_diag_wait_timeout": (I, [P, I, VP]),
         "probe_get_stats": (I, [P, C.POINTER(probe_stats)]),
         "probe_sizes": (I, [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(I),
                             C.POINTER(I), C.POINTER(I)]),
@@ -96,6 +99,7 @@ probe_apply_precond = lib.probe_apply_precond
 probe_forward_nonlinear = lib.probe_forward_nonlinear
 probe_gradient = lib.probe_gradient
 probe_set_option = lib.probe_set_option
+probe_diag_wait_timeout = lib.probe_diag_wait_timeout
 probe_get_stats = lib.probe_get_stats
 probe_sizes = lib.probe_sizes
 probe_last_error = lib.probe_last_error

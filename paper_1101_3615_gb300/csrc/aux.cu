@@ -278,4 +278,23 @@ cudaError_t launch_scale_copy(const float* src, float* dst, long long n, float a
     return cudaGetLastError();
 }
 
+// Diagnostic: one CTA waits on an mbarrier phase that nothing ever completes, so
+// the bounded wait can only end by its time limit; the kernel then records the
+// timeout in the device error word and returns (the context stays usable).
+__global__ void k_diag_wait(int* err, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (!ok && threadIdx.x == 0) set_dev_error(err, DEVERR_TIMEOUT);
+}
+
+cudaError_t launch_diag_wait(int* err, unsigned long long limit_ns, cudaStream_t st) {
+    k_diag_wait<<<1, 32, 0, st>>>(err, limit_ns);
+    return cudaGetLastError();
+}
+
 }  // namespace probe

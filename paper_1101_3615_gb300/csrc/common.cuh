@@ -40,6 +40,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
+// Plain arrival (no transaction bytes) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -52,18 +57,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for phase `parity` of `bar`; false if it did not complete within the limit.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Wait for phase `parity` of `bar`; false if it did not complete within `limit_ns`.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
     return true;
 }
 
 // 3D tiled TMA load of one box into shared memory, completing on `bar`.
 // The innermost coordinate x must be a multiple of 4 (16 bytes of FP32).
+// Rounding-explicit pieces of the explicit time update u^{n+1} = G (2 u^n - a- u^{n-1} + rhs)
+// (Sec. 2 scheme with the sponge).  Every product and sum is one IEEE operation written
+// out, so the compiler cannot fuse them differently in different kernel instantiations:
+// all 2D variants (one tile per CTA, pipelined, single- or multi-model) give the same bits.
+__device__ __forceinline__ float leapfrog(float G, float c, float am, float prev, float rhs) {
+    return __fmul_rn(G, __fadd_rn(__fmaf_rn(-am, prev, __fadd_rn(c, c)), rhs));
+}
+
+// G = 1 / (1 + e) and a- = 1 - e of a sponge cell; left at 1 where e = 0.
+__device__ __forceinline__ void sponge_pair(float e, float& G, float& am) {
+    if (e != 0.f) {
+        G = __frcp_rn(__fadd_rn(1.f, e));
+        am = __fsub_rn(1.f, e);
+    }
+}
+
 __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* map, int x, int y,
                                             int z, uint64_t* bar) {
     asm volatile(

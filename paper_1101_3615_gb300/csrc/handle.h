@@ -15,6 +15,8 @@ namespace probe {
 struct Workspace {
     // sizing key
     int W = 0, nb = 0, with_ckpt = 0, with_data = 0, groups = 0;
+    int history = 0;          // Dtt u^n kept for every step (no checkpoints)
+    int dtt_slots = 0;        // Dtt planes per shot
     size_t bytes = 0;
     float* u = nullptr;       // [W][2][F]
     float* f = nullptr;       // [W][nb][2][F]
@@ -29,8 +31,21 @@ struct Workspace {
     float* s_tmp = nullptr;   // [F]
     int* src_wave = nullptr;  // [W][2] padded sources of the wave
     CUtensorMap tm_u, tm_f;
+    CUtensorMap tm_up, tm_fp, tm_dmp, tm_dtp;  // plain 64 x 16 boxes (pipelined kernels)
     int tm_tile_z = 0;
     long long generation = 0;
+};
+
+// A captured sweep (forward + adjoint of one wave) and the key it was captured for.
+struct TunedEntry {
+    std::vector<long long> key;  // kind, adjoint, then shots and trials of each model (and handles for groups)
+    int pipe_fwd = 2, pipe_adj = 2, group = 4;
+};
+
+struct GraphEntry {
+    std::vector<long long> key;
+    cudaGraphExec_t exec = nullptr;
+    long long counts[4] = {0, 0, 0, 0};  // kernel launches inside (forward, recompute, adjoint, other)
 };
 
 struct DevBuf {
@@ -69,10 +84,19 @@ struct probe_s {
     probe::DevBuf stage_in, stage_out;
     // options
     int opt_check_finite = 1, opt_shot_wave = 0, opt_shot_group = 0, opt_use_graph = 0;
-    int opt_timing = 0, opt_tile_z = 0;
+    int opt_timing = 0, opt_tile_z = 0, opt_pipeline = 2, opt_dtt_history = 0;
+    int opt_autotune = 1;        // time the kernel variants on first use of a shape
+    int pipe_adj = 2;            // adjoint kernel variant (the forward uses opt_pipeline)
+    int user_fixed = 0;          // the caller chose pipeline / shot group: no autotuning
+    std::vector<probe::TunedEntry> tuned;  // autotuner results by workload key
     probe_stats stats{};
     std::vector<cudaEvent_t> events;
     probe::FitCache* fit = nullptr;  // FFT plans and buffers of probe_fit / probe_apply_precond
+    // captured sweeps (PROBE_OPT_USE_GRAPH), replayed on gstream
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+    std::vector<probe::GraphEntry> graphs;
+    long long graph_generation = -1;
 };
 
 namespace probe {

@@ -27,11 +27,19 @@ constexpr int kZC3D = 32;      // 3D planes marched by one CTA
 // space.
 // ---------------------------------------------------------------------------
 struct alignas(128) ModelStep2D {
-    CUtensorMap tm_u;  // incident-field planes  [W*2][Nz][P]
-    CUtensorMap tm_f;  // Born / adjoint planes  [W*nb*2][Nz][P]
+    CUtensorMap tm_u;    // incident-field planes  [W*2][Nz][P], halo box (64+8) x (TZ+8)
+    CUtensorMap tm_f;    // Born / adjoint planes  [W*nb*2][Nz][P], halo box
+    CUtensorMap tm_up;   // the same planes with a plain 64 x 16 box (pipelined kernels)
+    CUtensorMap tm_fp;
+    CUtensorMap tm_sp;   // s, one plane, plain box
+    CUtensorMap tm_dmp;  // dm, nb planes, plain box
+    CUtensorMap tm_dtp;  // Dtt segment buffer, W * dtt_slots planes, plain box
     int Nz, Nx, P, pad, nz, nx;
     int tiles_x, tiles_z, ntiles;
     int block_begin;   // first grid.z index of this model in the launch
+    int item_begin;    // pipelined kernels: first work item of this model
+    int dtt_slots;     // Dtt planes per shot in the segment buffer
+    int dtt_store;     // forward Born step also writes Dtt u^n to slot dtt_slot (history mode)
     int chunk;         // adjoint: trial chunk of this launch
     int nshots;        // shots resident in this launch
     int nb;            // trials (Born / adjoint fields per shot)
@@ -68,6 +76,7 @@ struct alignas(128) ModelStep2D {
 
 struct StepParams2D {
     int nmodels;
+    int total_items;  // pipelined kernels: work items over all models
     int n;    // time index of the step (forward: u^n -> u^{n+1}; adjoint: computes mu^n)
     int nt;
     int* err; // device error word
@@ -126,6 +135,11 @@ cudaError_t launch_fwd2d(FwdKind kind, int tile_z, const StepParams2D& p, int bl
 cudaError_t launch_adj2d(int tile_z, int nbc, bool kahan, const StepParams2D& p, int blocks,
                          int chunks, cudaStream_t st);
 size_t fwd2d_smem_bytes(FwdKind kind, int tile_z);
+// Pipelined persistent variants (stencil2d_pipe.cu), tile height kPipeTZ, `stages`-deep TMA ring.
+constexpr int kPipeTZ = 16;
+cudaError_t launch_fwd2d_pipe(FwdKind kind, int stages, const StepParams2D& p, cudaStream_t st);
+cudaError_t launch_adj2d_pipe(int nbc, bool kahan, int stages, const StepParams2D& p, int chunks, cudaStream_t st);
+size_t pipe_smem_bytes(int stages, bool adjoint);
 size_t adj2d_smem_bytes(int tile_z);
 cudaError_t stencil2d_configure();  // opt-in shared memory sizes
 
@@ -152,5 +166,6 @@ cudaError_t launch_encode_ckpt(const float* state, int nplanes, long long F, int
 cudaError_t launch_decode_ckpt(const void* src, const float* scales, int nplanes, long long F,
                                int pc, int dtype, float* state, cudaStream_t st);
 cudaError_t launch_scale_copy(const float* src, float* dst, long long n, float a, cudaStream_t st);
+cudaError_t launch_diag_wait(int* err, unsigned long long limit_ns, cudaStream_t st);
 
 }  // namespace probe

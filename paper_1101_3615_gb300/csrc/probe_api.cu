@@ -17,9 +17,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -118,23 +120,46 @@ probe_status encode_planes(probe_t h, CUtensorMap* map, float* base, int planes,
     return PROBE_OK;
 }
 
+// 2D FP32 tensor map over `planes` planes with a plain 64 x 16 box (no halo).
+probe_status encode_plain(probe_t h, CUtensorMap* map, const float* base, int planes) {
+    TRY(get_encoder(h));
+    cuuint32_t es[3] = {1, 1, 1};
+    cuuint64_t dims[3] = {(cuuint64_t)h->Nx, (cuuint64_t)h->Nz, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)h->P * 4, (cuuint64_t)h->F * 4};
+    cuuint32_t box[3] = {(cuuint32_t)kTX, (cuuint32_t)kPipeTZ, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(h, PROBE_ERR_CUDA, "cuTensorMapEncodeTiled (plain box) failed (" + std::to_string((int)r) + ")");
+    return PROBE_OK;
+}
+
+// Workspace generations are unique in the process, so a cached graph keyed by
+// (handle, generation) can never match a later workspace at reused addresses.
+std::atomic<long long> g_generation{0};
+
 void free_ws(Workspace& w) {
     void* ptrs[] = {w.u, w.f, w.dm, w.data, w.ckpt, w.scales, w.absmax, w.dtt, w.img, w.comp, w.s_tmp,
                     w.src_wave};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    long long gen = w.generation;
     w = Workspace();
-    w.generation = gen + 1;
+    w.generation = ++g_generation;
 }
 
 size_t snap_bytes(int snap) { return snap == PROBE_SNAP_FP32 ? 4 : 2; }
 
 // Bytes per resident shot and fixed bytes of a job with nb trials.
+bool use_history(probe_t h, int with_ckpt) { return with_ckpt && h->opt_dtt_history && h->ndim == 2; }
+
 void ws_bytes(probe_t h, int nb, int with_ckpt, int with_data, double* per_shot, double* fixed) {
     const double F4 = (double)h->F * 4.0;
     double ps = 2 * F4 + 2.0 * nb * F4;
-    if (with_ckpt) ps += (double)h->nck * 2 * h->F * snap_bytes(h->snap) + (double)h->K * F4 + 16.0 * h->nck;
+    if (use_history(h, with_ckpt))
+        ps += (double)(h->nt - 1) * F4;
+    else if (with_ckpt)
+        ps += (double)h->nck * 2 * h->F * snap_bytes(h->snap) + (double)h->K * F4 + 16.0 * h->nck;
     if (with_data) ps += (double)nb * h->nt * h->nr * 4.0;
     if (h->ndim == 3 && with_ckpt) ps += 2.0 * nb * F4;  // per-shot images + compensation
     *per_shot = ps;
@@ -160,9 +185,10 @@ int pick_group(probe_t h, int W) {
 
 probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     Workspace& w = h->ws;
-    const int G = (W + pick_group(h, W) - 1) / pick_group(h, W);
+    const int G = W;  // image groups for the smallest shot group: any group size fits
+    const int history = use_history(h, with_ckpt) ? 1 : 0;
     if (w.u && w.W >= W && w.nb >= nb && w.with_ckpt >= with_ckpt && w.with_data >= with_data &&
-        w.groups >= G && w.tm_tile_z == h->tile_z && w.W == W && w.nb == nb)
+        w.groups >= G && w.tm_tile_z == h->tile_z && w.W == W && w.nb == nb && w.history == history)
         return PROBE_OK;
     free_ws(w);
     const long long F = h->F;
@@ -180,7 +206,9 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     TRY(alloc((void**)&w.f, (size_t)W * std::max(nb, 1) * 2 * F * 4));
     TRY(alloc((void**)&w.dm, (size_t)std::max(nb, 1) * F * 4));
     if (with_data) TRY(alloc((void**)&w.data, (size_t)W * nb * h->nt * h->nr * 4));
-    if (with_ckpt) {
+    if (history) {
+        TRY(alloc((void**)&w.dtt, (size_t)W * (h->nt - 1) * F * 4));  // Dtt u^n of every step
+    } else if (with_ckpt) {
         TRY(alloc(&w.ckpt, (size_t)h->nck * W * 2 * F * snap_bytes(h->snap)));
         TRY(alloc((void**)&w.scales, (size_t)h->nck * W * 2 * 4));
         TRY(alloc((void**)&w.absmax, (size_t)W * 2 * 4));
@@ -195,7 +223,9 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     // field planes must read as zero outside what the kernels write
     CK(h, cudaMemset(w.u, 0, (size_t)W * 2 * F * 4));
     CK(h, cudaMemset(w.f, 0, (size_t)W * std::max(nb, 1) * 2 * F * 4));
-    if (w.dtt) CK(h, cudaMemset(w.dtt, 0, (size_t)W * (with_ckpt ? h->K : 1) * F * 4));
+    w.history = history;
+    w.dtt_slots = history ? h->nt - 1 : (with_ckpt ? h->K : 1);
+    if (w.dtt) CK(h, cudaMemset(w.dtt, 0, (size_t)W * w.dtt_slots * F * 4));
     w.W = W;
     w.nb = nb;
     w.with_ckpt = with_ckpt;
@@ -203,6 +233,12 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     w.groups = G;
     TRY(encode_planes(h, &w.tm_u, w.u, W * 2, h->tile_z));
     TRY(encode_planes(h, &w.tm_f, w.f, W * std::max(nb, 1) * 2, h->tile_z));
+    if (h->ndim == 2) {
+        TRY(encode_plain(h, &w.tm_up, w.u, W * 2));
+        TRY(encode_plain(h, &w.tm_fp, w.f, W * std::max(nb, 1) * 2));
+        TRY(encode_plain(h, &w.tm_dmp, w.dm, std::max(nb, 1)));
+        if (w.dtt) TRY(encode_plain(h, &w.tm_dtp, w.dtt, W * w.dtt_slots));
+    }
     w.tm_tile_z = h->tile_z;
     return PROBE_OK;
 }
@@ -260,12 +296,12 @@ probe_status set_tile_z(probe_t h, int tz) {
 // ---------------------------------------------------------------------------
 struct Job {
     probe_t h;
-    int j0, W, nb;
-    const float* s;
-    float* data;          // forward output (Born or incident traces), may be null
-    const float* rdata;   // adjoint input
-    long long dss, dts;   // data strides: shot, trial
-    int groups, shot_group;
+    int j0 = 0, W = 0, nb = 0;
+    const float* s = nullptr;
+    float* data = nullptr;          // forward output (Born or incident traces), may be null
+    const float* rdata = nullptr;   // adjoint input
+    long long dss = 0, dts = 0;     // data strides: shot, trial
+    int groups = 1, shot_group = 1;
 };
 
 void fill_model(const Job& jb, ModelStep2D& m, int* blocks_fwd, int* blocks_adj) {
@@ -273,6 +309,13 @@ void fill_model(const Job& jb, ModelStep2D& m, int* blocks_fwd, int* blocks_adj)
     Workspace& w = h->ws;
     m.tm_u = w.tm_u;
     m.tm_f = w.tm_f;
+    m.tm_up = w.tm_up;
+    m.tm_fp = w.tm_fp;
+    m.tm_dmp = w.tm_dmp;
+    m.tm_dtp = w.tm_dtp;
+    m.dtt_slots = w.dtt_slots;
+    m.dtt_store = w.history;
+    if (encode_plain(h, &m.tm_sp, jb.s, 1) != PROBE_OK) m.s = nullptr;
     m.Nz = h->Nz;
     m.Nx = h->Nx;
     m.P = h->P;
@@ -310,7 +353,7 @@ void fill_model(const Job& jb, ModelStep2D& m, int* blocks_fwd, int* blocks_adj)
     m.s = jb.s;
     m.dm = w.dm;
     m.dtt = w.dtt;
-    m.dtt_shot_stride = (long long)h->K * h->F;
+    m.dtt_shot_stride = (long long)w.dtt_slots * h->F;
     m.wavelet = h->d_wavelet;
     m.src_zx = w.src_wave;
     m.rec_tile_ptr = h->d_rec_tile_ptr;
@@ -333,6 +376,8 @@ struct Sweep {
     int blocks_fwd = 0, blocks_adj = 0;
     int nbc = 1, chunks = 1;
     int tile_z = 16;
+    int pipeline = 0;      // forward: 0 one tile per CTA; 2..4 persistent pipelined kernels
+    int pipeline_adj = 0;  // adjoint variant
     bool kahan = true;
     cudaStream_t st = nullptr;
     int nt = 0, K = 0, nck = 0;
@@ -349,6 +394,8 @@ probe_status prepare_sweep(Sweep& sw, probe_t h0, cudaStream_t st) {
     sw.K = h0->K;
     sw.nck = h0->nck;
     sw.tile_z = h0->tile_z;
+    sw.pipeline = h0->opt_pipeline;
+    sw.pipeline_adj = h0->pipe_adj;
     sw.kahan = h0->kahan != 0;
     int maxnb = 1;
     std::vector<int> bf(sw.jobs.size()), ba(sw.jobs.size());
@@ -373,19 +420,24 @@ probe_status prepare_sweep(Sweep& sw, probe_t h0, cudaStream_t st) {
 }
 
 void set_grid(Sweep& sw, bool adjoint) {
-    int b = 0;
+    int b = 0, items = 0;
     for (size_t k = 0; k < sw.jobs.size(); ++k) {
-        sw.p.m[k].block_begin = b;
         const Job& jb = sw.jobs[k];
-        b += adjoint ? jb.groups : jb.W;
+        const int units = adjoint ? jb.groups : jb.W;
+        sw.p.m[k].block_begin = b;
+        sw.p.m[k].item_begin = items;
+        b += units;
+        items += units * jb.h->ntiles;
     }
+    sw.p.total_items = items;
 }
 
 probe_status launch_fwd_step(Sweep& sw, FwdKind kind, int n, int slot) {
     set_grid(sw, false);
     sw.p.n = n;
     for (int k = 0; k < sw.p.nmodels; ++k) sw.p.m[k].dtt_slot = slot;
-    cudaError_t e = launch_fwd2d(kind, sw.tile_z, sw.p, sw.blocks_fwd, sw.st);
+    cudaError_t e = (sw.pipeline && sw.tile_z == kPipeTZ) ? launch_fwd2d_pipe(kind, sw.pipeline, sw.p, sw.st)
+                                                           : launch_fwd2d(kind, sw.tile_z, sw.p, sw.blocks_fwd, sw.st);
     if (e != cudaSuccess) return cuda_fail(sw.jobs[0].h, e, "forward step launch");
     return PROBE_OK;
 }
@@ -394,7 +446,9 @@ probe_status launch_adj_step(Sweep& sw, int n, int slot) {
     set_grid(sw, true);
     sw.p.n = n;
     for (int k = 0; k < sw.p.nmodels; ++k) sw.p.m[k].dtt_slot = slot;
-    cudaError_t e = launch_adj2d(sw.tile_z, sw.nbc, sw.kahan, sw.p, sw.blocks_adj, sw.chunks, sw.st);
+    cudaError_t e = (sw.pipeline_adj && sw.tile_z == kPipeTZ)
+                        ? launch_adj2d_pipe(sw.nbc, sw.kahan, sw.pipeline_adj, sw.p, sw.chunks, sw.st)
+                        : launch_adj2d(sw.tile_z, sw.nbc, sw.kahan, sw.p, sw.blocks_adj, sw.chunks, sw.st);
     if (e != cudaSuccess) return cuda_fail(sw.jobs[0].h, e, "adjoint step launch");
     return PROBE_OK;
 }
@@ -411,8 +465,10 @@ probe_status run_forward(Sweep& sw, FwdKind kind, bool ckpt) {
         if (kind == FWD_BORN)
             CK(jb.h, cudaMemsetAsync(w.f, 0, (size_t)jb.W * jb.nb * 2 * jb.h->F * 4, sw.st));
     }
+    const bool history = sw.jobs[0].h->ws.history != 0;
+    if (history && kind == FWD_INCIDENT) kind = FWD_INCIDENT_DTT;  // Dtt u^n of every step
     for (int n = 0; n < sw.nt - 1; ++n) {
-        if (ckpt && n % sw.K == 0) {
+        if (ckpt && !history && n % sw.K == 0) {
             for (Job& jb : sw.jobs) {
                 Workspace& w = jb.h->ws;
                 const int k = n / sw.K;
@@ -424,7 +480,7 @@ probe_status run_forward(Sweep& sw, FwdKind kind, bool ckpt) {
                 sw.launches_other += (jb.h->snap == PROBE_SNAP_FP32) ? 0 : 2;
             }
         }
-        TRY(launch_fwd_step(sw, kind, n, 0));
+        TRY(launch_fwd_step(sw, kind, n, history ? n : 0));
         sw.launches_fwd++;
     }
     // last time level at the receivers
@@ -452,6 +508,16 @@ probe_status run_adjoint(Sweep& sw) {
     }
     probe_t h0 = sw.jobs[0].h;
     int ev = 2;
+    if (h0->ws.history) {  // Dtt u^n kept for every step: no recomputation
+        record(h0, ev++, sw.st);
+        record(h0, ev++, sw.st);
+        for (int n = sw.nt - 1; n >= 1; --n) {
+            TRY(launch_adj_step(sw, n, n - 1));
+            sw.launches_adj += sw.chunks;
+        }
+        record(h0, ev++, sw.st);
+        return PROBE_OK;
+    }
     for (int k = sw.nck - 1; k >= 0; --k) {
         const int k0 = k * sw.K;
         const int k1 = std::min(k0 + sw.K, sw.nt - 1);
@@ -657,6 +723,69 @@ probe_status check_dev_error(probe_t h, cudaStream_t st) {
     return PROBE_OK;
 }
 
+void clear_graphs(probe_t h) {
+    for (GraphEntry& g : h->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
+probe_status ensure_graph_stream(probe_t h) {
+    if (h->gstream) return PROBE_OK;
+    CK(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+    CK(h, cudaEventCreateWithFlags(&h->gev_in, cudaEventDisableTiming));
+    CK(h, cudaEventCreateWithFlags(&h->gev_out, cudaEventDisableTiming));
+    return PROBE_OK;
+}
+
+// Run `body(stream)` for one wave either eagerly on `st` or as a cached CUDA graph
+// (captured once per key on the library stream and replayed there, joined to `st`
+// by events).
+template <typename Body>
+probe_status run_maybe_graph(probe_t h, const std::vector<long long>& key, cudaStream_t st, long long counts[4],
+                             Body body) {
+    if (!h->opt_use_graph || h->opt_timing) return body(st);
+    TRY(ensure_graph_stream(h));
+    if (h->graph_generation != h->ws.generation) {
+        clear_graphs(h);
+        h->graph_generation = h->ws.generation;
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (GraphEntry& g : h->graphs)
+        if (g.key == key) {
+            exec = g.exec;
+            for (int i = 0; i < 4; ++i) counts[i] = g.counts[i];
+        }
+    if (!exec) {
+        CK(h, cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal));
+        probe_status s = body(h->gstream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->gstream, &graph);
+        if (s != PROBE_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+        if (h->graphs.size() >= 16) {
+            cudaGraphExecDestroy(h->graphs.front().exec);
+            h->graphs.erase(h->graphs.begin());
+        }
+        GraphEntry g;
+        g.key = key;
+        g.exec = exec;
+        for (int i = 0; i < 4; ++i) g.counts[i] = counts[i];
+        h->graphs.push_back(g);
+    }
+    CK(h, cudaEventRecord(h->gev_in, st));
+    CK(h, cudaStreamWaitEvent(h->gstream, h->gev_in, 0));
+    CK(h, cudaGraphLaunch(exec, h->gstream));
+    CK(h, cudaEventRecord(h->gev_out, h->gstream));
+    CK(h, cudaStreamWaitEvent(st, h->gev_out, 0));
+    return PROBE_OK;
+}
+
 // Stage an input array on the device (returns a device pointer).
 probe_status stage_input(probe_t h, const float* p, size_t n, DevBuf& buf, const float** out,
                          cudaStream_t st, bool* was_host) {
@@ -676,6 +805,7 @@ void reset_stats(probe_t h) {
     h->stats = probe_stats();
     h->stats.ckpt_stride = h->K;
     h->stats.tile_z = h->tile_z;
+    h->stats.dtt_history = h->ws.history;
 }
 
 void finish_stats(probe_t h, const Sweep& sw, int nwaves_events) {
@@ -853,6 +983,10 @@ extern "C" probe_status probe_create(probe_t* out, const probe_grid* g, const fl
 
 extern "C" void probe_destroy(probe_t h) {
     if (!h) return;
+    clear_graphs(h);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
+    if (h->gev_in) cudaEventDestroy(h->gev_in);
+    if (h->gev_out) cudaEventDestroy(h->gev_out);
     fit_cache_destroy(h);
     free_ws(h->ws);
     void* ptrs[] = {h->d_m0, h->d_s0, h->d_wavelet, h->d_src, h->d_rec, h->d_rec_tile_ptr, h->d_rec_tile_idx,
@@ -889,16 +1023,38 @@ extern "C" probe_status probe_set_option(probe_t h, int key, long long v) {
         case PROBE_OPT_SHOT_GROUP:
             if (v < 0) return fail(h, PROBE_ERR_ARG, "shot group must be >= 0");
             h->opt_shot_group = (int)v;
-            free_ws(h->ws);
+            h->user_fixed = 1;
+            return PROBE_OK;
+        case PROBE_OPT_AUTOTUNE:
+            h->opt_autotune = v ? 1 : 0;
             return PROBE_OK;
         case PROBE_OPT_USE_GRAPH: h->opt_use_graph = v ? 1 : 0; return PROBE_OK;
         case PROBE_OPT_TIMING: h->opt_timing = v ? 1 : 0; return PROBE_OK;
+        case PROBE_OPT_DTT_HISTORY:
+            h->opt_dtt_history = v ? 1 : 0;
+            free_ws(h->ws);
+            return PROBE_OK;
+        case PROBE_OPT_PIPELINE:
+            if (v != 0 && (v < 2 || v > 4)) return fail(h, PROBE_ERR_ARG, "pipeline must be 0, 2, 3 or 4");
+            h->opt_pipeline = (int)v;
+            h->pipe_adj = (int)v;
+            h->user_fixed = 1;
+            return PROBE_OK;
         case PROBE_OPT_TILE_Z:
             if (v != 0 && v != 16 && v != 32) return fail(h, PROBE_ERR_ARG, "tile_z must be 0, 16 or 32");
             h->opt_tile_z = (int)v;
             return set_tile_z(h, v ? (int)v : 16);
     }
     return fail(h, PROBE_ERR_ARG, "unknown option");
+}
+
+extern "C" probe_status probe_diag_wait_timeout(probe_t h, int timeout_ms, probe_stream_t stream) {
+    if (!h) return PROBE_ERR_ARG;
+    if (timeout_ms < 1 || timeout_ms > 10000) return fail(h, PROBE_ERR_ARG, "timeout_ms must be in [1, 10000]");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_diag_wait(h->d_err, (unsigned long long)timeout_ms * 1000000ull, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostic wait launch");
+    return check_dev_error(h, st);
 }
 
 extern "C" probe_status probe_get_stats(probe_t h, probe_stats* out) {
@@ -932,6 +1088,98 @@ double elapsed(probe_t h, int a, int b) {
     return ms;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: time a few steps of each kernel variant on the real workspace.
+// ---------------------------------------------------------------------------
+probe_status time_steps(probe_t h, cudaStream_t st, float* ms, const std::function<probe_status()>& step, int reps) {
+    TRY(ensure_events(h, 2));
+    TRY(step());  // warm-up (also configures the kernel)
+    CK(h, cudaEventRecord(h->events[0], st));
+    for (int i = 0; i < reps; ++i) TRY(step());
+    CK(h, cudaEventRecord(h->events[1], st));
+    CK(h, cudaEventSynchronize(h->events[1]));
+    CK(h, cudaEventElapsedTime(ms, h->events[0], h->events[1]));
+    return PROBE_OK;
+}
+
+// base: the jobs of the first shot wave (one per model), exactly as the sweep will
+// run them (source positions uploaded, data pointers set).  Forward variants are
+// timed at step 0 and adjoint variants at step nt-1, the first step each sweep
+// computes, so whatever the trial launches write is written again by the sweep.
+// The result (forward variant, adjoint variant, shots per adjoint CTA) is kept on
+// h under key; *group receives the shot group (0: keep each handle's own).
+probe_status autotune_2d(probe_t h, const std::vector<long long>& key, std::vector<Job> base, FwdKind kind,
+                         bool adjoint, bool time_it, cudaStream_t st, int* group) {
+    *group = 0;
+    if (!h->opt_autotune || h->user_fixed || h->ndim != 2 || h->tile_z != kPipeTZ || h->nt < 3) return PROBE_OK;
+    for (const TunedEntry& t : h->tuned)
+        if (t.key == key) {
+            h->opt_pipeline = t.pipe_fwd;
+            h->pipe_adj = t.pipe_adj;
+            *group = t.group;
+            return PROBE_OK;
+        }
+    if (!time_it) return PROBE_OK;
+    int maxW = 1;
+    for (const Job& jb : base) maxW = std::max(maxW, jb.W);
+    const int saved_timing = h->opt_timing;
+    h->opt_timing = 0;
+    auto sweep_for = [&](int shot_group, Sweep* sw) {
+        sw->jobs = base;
+        for (Job& jb : sw->jobs) {
+            jb.shot_group = std::min(shot_group, jb.W);
+            jb.groups = (jb.W + jb.shot_group - 1) / jb.shot_group;
+        }
+        return prepare_sweep(*sw, h, st);
+    };
+    probe_status rc = PROBE_OK;
+    int best_fwd = h->opt_pipeline, best_adj = h->pipe_adj, best_grp = std::min(4, maxW);
+    float best = 1e30f;
+    for (int pipe : {0, 2, 3}) {
+        h->opt_pipeline = pipe;
+        Sweep sw;
+        float ms = 0.f;
+        if ((rc = sweep_for(1, &sw)) != PROBE_OK) break;
+        if ((rc = time_steps(h, st, &ms, [&]() { return launch_fwd_step(sw, kind, 0, 0); }, 16)) != PROBE_OK) break;
+        if (ms < best) {
+            best = ms;
+            best_fwd = pipe;
+        }
+    }
+    if (rc == PROBE_OK && adjoint) {
+        best = 1e30f;
+        for (int pipe : {0, 2}) {
+            for (int grp : {1, 2, 4, 8}) {
+                if (grp > 1 && grp >= 2 * maxW) continue;
+                h->pipe_adj = pipe;
+                Sweep sw;
+                float ms = 0.f;
+                if ((rc = sweep_for(grp, &sw)) != PROBE_OK) break;
+                if ((rc = time_steps(h, st, &ms, [&]() { return launch_adj_step(sw, h->nt - 1, 0); }, 16)) != PROBE_OK)
+                    break;
+                if (ms < best) {
+                    best = ms;
+                    best_adj = pipe;
+                    best_grp = grp;
+                }
+            }
+            if (rc != PROBE_OK) break;
+        }
+    }
+    h->opt_timing = saved_timing;
+    h->opt_pipeline = best_fwd;
+    h->pipe_adj = best_adj;
+    if (rc != PROBE_OK) return rc;
+    *group = best_grp;
+    TunedEntry t;
+    t.key = key;
+    t.pipe_fwd = best_fwd;
+    t.pipe_adj = best_adj;
+    t.group = best_grp;
+    h->tuned.push_back(t);
+    return PROBE_OK;
+}
+
 // Run one operator on one model.  dm: device [nb][n]; data_user: device [nb][ns][nt][nr] (F / F*)
 // or [ns][nt][nr] (nonlinear / gradient); img_out: device [nb][n].
 probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in, float* data_out,
@@ -942,19 +1190,14 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
     const int W = plan_wave(h, nbw, need_ckpt, need_data);
     TRY(ensure_ws(h, W, nbw, need_ckpt, need_data));
     Workspace& w = h->ws;
-    const int G = w.groups;
+    int G = 0;
     reset_stats(h);
     h->stats.shot_wave = W;
-    h->stats.shot_group = pick_group(h, W);
     if (op == OP_F || op == OP_H) {
         CK(h, cudaMemsetAsync(w.dm, 0, (size_t)nb * h->F * 4, st));
         cudaError_t e = launch_embed(dm_dev, w.dm, nb, h->nz, h->nx, h->ny, h->pad, h->Nz, h->Nx, h->Ny, h->P,
                                      h->F, 1.0f, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "embed dm");
-    }
-    if (need_ckpt) {
-        CK(h, cudaMemsetAsync(w.img, 0, (size_t)G * nbw * h->F * 4, st));
-        CK(h, cudaMemsetAsync(w.comp, 0, (size_t)G * nbw * h->F * 4, st));
     }
     const int nwaves = (h->ns + W - 1) / W;
     const int nev = 3 + 2 * h->nck + 2;
@@ -972,8 +1215,6 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
         jb.W = Wv;
         jb.nb = nbw;
         jb.s = s;
-        jb.shot_group = pick_group(h, W);
-        jb.groups = (Wv + jb.shot_group - 1) / jb.shot_group;
         const long long tr = (long long)h->nt * h->nr;
         switch (op) {
             case OP_F:
@@ -1006,6 +1247,28 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
         FwdKind kind = (op == OP_F || op == OP_H) ? FWD_BORN
                        : (op == OP_NONLIN)        ? FWD_INCIDENT_SAMPLE
                                                   : FWD_INCIDENT;
+        if (wv == 0) {
+            if (h->ndim == 2) {
+                jb.shot_group = pick_group(h, W);
+                jb.groups = (Wv + jb.shot_group - 1) / jb.shot_group;
+                // the Born and adjoint sweeps are timed; F and the nonlinear forward reuse a result
+                const std::vector<long long> tkey = {(long long)kind, (long long)need_ckpt, Wv, nbw};
+                int grp = 0;
+                TRY(autotune_2d(h, tkey, {jb}, kind, need_ckpt, op == OP_H || need_ckpt, st, &grp));
+                if (grp > 0) h->opt_shot_group = grp;
+            }
+            G = (W + pick_group(h, W) - 1) / pick_group(h, W);
+            h->stats.shot_group = pick_group(h, W);
+            const bool piped = h->ndim == 2 && h->tile_z == kPipeTZ;
+            h->stats.pipeline_forward = piped ? h->opt_pipeline : 0;
+            h->stats.pipeline_adjoint = piped ? h->pipe_adj : 0;
+            if (need_ckpt) {
+                CK(h, cudaMemsetAsync(w.img, 0, (size_t)G * nbw * h->F * 4, st));
+                CK(h, cudaMemsetAsync(w.comp, 0, (size_t)G * nbw * h->F * 4, st));
+            }
+        }
+        jb.shot_group = pick_group(h, W);
+        jb.groups = (Wv + jb.shot_group - 1) / jb.shot_group;
         if (h->ndim == 3) {
             Count3 c3;
             record(h, 0, st);
@@ -1018,11 +1281,29 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
             h->stats.launches_total += c3.fwd + c3.rec + c3.adj + c3.other;
         } else {
             sw.jobs.push_back(jb);
-            TRY(prepare_sweep(sw, h, st));
-            record(h, 0, st);
-            TRY(run_forward(sw, kind, need_ckpt));
-            record(h, 1, st);
-            if (need_ckpt) TRY(run_adjoint(sw));
+            const std::vector<long long> key = {(long long)op, (long long)kind, (long long)need_ckpt, Wv, nbw, j0,
+                                                (long long)(size_t)jb.data, (long long)(size_t)jb.rdata,
+                                                (long long)(size_t)jb.s, h->ws.generation, h->opt_pipeline, h->pipe_adj,
+                                                jb.shot_group, h->tile_z, h->nt};
+            long long cnt[4] = {0, 0, 0, 0};
+            TRY(run_maybe_graph(h, key, st, cnt, [&](cudaStream_t ss) -> probe_status {
+                Sweep sw2;
+                sw2.jobs = sw.jobs;
+                TRY(prepare_sweep(sw2, h, ss));
+                record(h, 0, ss);
+                TRY(run_forward(sw2, kind, need_ckpt));
+                record(h, 1, ss);
+                if (need_ckpt) TRY(run_adjoint(sw2));
+                cnt[0] = sw2.launches_fwd;
+                cnt[1] = sw2.launches_rec;
+                cnt[2] = sw2.launches_adj;
+                cnt[3] = sw2.launches_other;
+                return PROBE_OK;
+            }));
+            sw.launches_fwd = cnt[0];
+            sw.launches_rec = cnt[1];
+            sw.launches_adj = cnt[2];
+            sw.launches_other = cnt[3];
             finish_stats(h, sw, nwaves);
         }
         const double cells = (double)h->Nz * h->Ny * h->Nx;
@@ -1031,11 +1312,15 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
         h->stats.cell_updates_forward += cells * steps * Wv * nfields;
         // algorithmic bytes: incident 16 B (u^n, u^{n-1}, s, write), Born +16 B per trial
         // (du^n, du^{n-1}, dm, write); +4 B Dtt write in the recompute
-        h->stats.bytes_forward += cells * steps * Wv * (16.0 + (kind == FWD_BORN ? 16.0 * nbw : 0.0));
+        const bool hist = w.history != 0;
+        h->stats.bytes_forward += cells * steps * Wv *
+                                  (16.0 + (kind == FWD_BORN ? 16.0 * nbw : 0.0) + (hist ? 4.0 : 0.0));
         if (need_ckpt) {
-            h->stats.cell_updates_recompute += cells * steps * Wv;
+            if (!hist) {
+                h->stats.cell_updates_recompute += cells * steps * Wv;
+                h->stats.bytes_recompute += cells * steps * Wv * 20.0;
+            }
             h->stats.cell_updates_adjoint += cells * steps * Wv * nbw;
-            h->stats.bytes_recompute += cells * steps * Wv * 20.0;
             // adjoint: per (shot, trial) mu^{n+1}, mu^{n+2}, write mu^n = 12 B; per shot Dtt 4 B;
             // s 4 B and image traffic per (group, trial) amortised over the group
             const double img_b = (h->kahan ? 16.0 : 8.0);
@@ -1045,7 +1330,9 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
         if (h->opt_timing) {
             CK(h, cudaStreamSynchronize(st));
             ms_f += elapsed(h, 0, 1);
-            if (need_ckpt) {
+            if (need_ckpt && hist) {
+                ms_a += elapsed(h, 3, 4);
+            } else if (need_ckpt) {
                 int ev = 2;
                 for (int k = h->nck - 1; k >= 0; --k) {
                     const int k0 = k * h->K, k1 = std::min(k0 + h->K, h->nt - 1);
@@ -1280,8 +1567,6 @@ extern "C" probe_status probe_apply_H_group(const probe_t* models, int nmodels, 
         CK(h, cudaMemsetAsync(w.dm, 0, (size_t)nb[k] * h->F * 4, st));
         cudaError_t e = launch_embed(dmd, w.dm, nb[k], h->nz, h->nx, 1, h->pad, h->Nz, h->Nx, 1, h->P, h->F, 1.0f, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "embed dm");
-        CK(h, cudaMemsetAsync(w.img, 0, (size_t)w.groups * nb[k] * h->F * 4, st));
-        CK(h, cudaMemsetAsync(w.comp, 0, (size_t)w.groups * nb[k] * h->F * 4, st));
         CK(h, cudaMemcpyAsync(w.src_wave, h->src_pad.data(), (size_t)h->ns * 2 * 4, cudaMemcpyHostToDevice, st));
         Job jb;
         jb.h = h;
@@ -1290,7 +1575,7 @@ extern "C" probe_status probe_apply_H_group(const probe_t* models, int nmodels, 
         jb.nb = nb[k];
         jb.s = h->d_s0;
         jb.shot_group = pick_group(h, h->ns);
-        jb.groups = w.groups;
+        jb.groups = (jb.W + jb.shot_group - 1) / jb.shot_group;
         const long long tr = (long long)h->nt * h->nr;
         jb.data = w.data;
         jb.rdata = w.data;
@@ -1298,17 +1583,60 @@ extern "C" probe_status probe_apply_H_group(const probe_t* models, int nmodels, 
         jb.dts = tr;
         sw.jobs.push_back(jb);
     }
-    TRY(prepare_sweep(sw, h0, st));
+    // kernel variants and shot group for this group of workloads (the result is kept on h0)
+    std::vector<long long> key = {-1, (long long)FWD_BORN, 1, nmodels};
+    for (const Job& jb : sw.jobs) {
+        key.push_back((long long)(size_t)jb.h);
+        key.push_back(jb.W);
+        key.push_back(jb.nb);
+    }
+    int grp = 0;
+    TRY(autotune_2d(h0, key, sw.jobs, FWD_BORN, true, true, st, &grp));
+    for (Job& jb : sw.jobs) {
+        if (grp > 0) jb.shot_group = std::min(grp, jb.W);
+        jb.groups = (jb.W + jb.shot_group - 1) / jb.shot_group;
+        Workspace& w = jb.h->ws;
+        CK(jb.h, cudaMemsetAsync(w.img, 0, (size_t)jb.groups * jb.nb * jb.h->F * 4, st));
+        CK(jb.h, cudaMemsetAsync(w.comp, 0, (size_t)jb.groups * jb.nb * jb.h->F * 4, st));
+    }
+    h0->stats.shot_group = sw.jobs[0].shot_group;
+    h0->stats.pipeline_forward = h0->tile_z == kPipeTZ ? h0->opt_pipeline : 0;
+    h0->stats.pipeline_adjoint = h0->tile_z == kPipeTZ ? h0->pipe_adj : 0;
     if (h0->opt_timing) TRY(ensure_events(h0, 3 + 2 * h0->nck + 2));
-    record(h0, 0, st);
-    TRY(run_forward(sw, FWD_BORN, true));
-    record(h0, 1, st);
-    TRY(run_adjoint(sw));
+    // the whole group's sweeps as one graph (cached on h0 by handles, workspaces and variants)
+    std::vector<long long> gkey = key;
+    for (const Job& jb : sw.jobs) {
+        gkey.push_back(jb.h->ws.generation);
+        gkey.push_back(jb.shot_group);
+    }
+    gkey.push_back(h0->opt_pipeline);
+    gkey.push_back(h0->pipe_adj);
+    gkey.push_back(h0->tile_z);
+    long long cnt[4] = {0, 0, 0, 0};
+    TRY(run_maybe_graph(h0, gkey, st, cnt, [&](cudaStream_t ss) -> probe_status {
+        Sweep sw2;
+        sw2.jobs = sw.jobs;
+        TRY(prepare_sweep(sw2, h0, ss));
+        record(h0, 0, ss);
+        TRY(run_forward(sw2, FWD_BORN, true));
+        record(h0, 1, ss);
+        TRY(run_adjoint(sw2));
+        cnt[0] = sw2.launches_fwd;
+        cnt[1] = sw2.launches_rec;
+        cnt[2] = sw2.launches_adj;
+        cnt[3] = sw2.launches_other;
+        return PROBE_OK;
+    }));
+    sw.launches_fwd = cnt[0];
+    sw.launches_rec = cnt[1];
+    sw.launches_adj = cnt[2];
+    sw.launches_other = cnt[3];
     finish_stats(h0, sw, 1);
     for (int k = 0; k < nmodels; ++k) {
         probe_t h = models[k];
         Workspace& w = h->ws;
-        cudaError_t e = launch_extract_images(w.img, w.comp, w.groups, (long long)nb[k] * h->F, nb[k], h->F, outs[k],
+        const int groups_k = sw.jobs[k].groups;
+        cudaError_t e = launch_extract_images(w.img, w.comp, groups_k, (long long)nb[k] * h->F, nb[k], h->F, outs[k],
                                               h->nz, 1, h->nx, h->pad, 1, h->P, h->kahan != 0, false, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "image extraction");
         const double cells = (double)h->Nz * h->Nx, steps = h->nt - 1;

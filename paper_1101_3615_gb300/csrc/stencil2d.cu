@@ -82,7 +82,12 @@ __device__ __forceinline__ void lap4(const float* t, int row, int col, const Mod
 __device__ __forceinline__ float sponge_e(const ModelStep2D& M, int z, int x) {
     const int rz = max(max(M.pad - z, z - (M.pad + M.nz - 1)), 0);
     const int rx = max(max(M.pad - x, x - (M.pad + M.nx - 1)), 0);
-    return M.cz * (float)(rz * rz) + M.cx * (float)(rx * rx);
+    return __fmaf_rn(M.cz, (float)(rz * rz), __fmul_rn(M.cx, (float)(rx * rx)));
+}
+
+// G = 1/(1 + e) and a- = 1 - e of a sponge cell (left at 1 where e = 0).
+__device__ __forceinline__ void sponge_factors(const ModelStep2D& M, int z, int x, float& G, float& am) {
+    sponge_pair(sponge_e(M, z, x), G, am);
 }
 
 // Record the receivers of this tile from a staged field tile.
@@ -174,7 +179,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd2d(const __grid_constant__ Step
 
     const int sz = M.src_zx[2 * shot], sx = M.src_zx[2 * shot + 1];
     const float fsrc = M.wavelet[n] * M.vol_inv;
-    float D[ROWS][4], Gc[ROWS][4], Am[ROWS][4];
+    float D[ROWS][4];
+    bool interior[ROWS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
         const int z = z0 + lz + 16 * r;
@@ -186,26 +192,18 @@ __global__ void __launch_bounds__(kThreads) k_fwd2d(const __grid_constant__ Step
             if (j >= 0 && j < 4) L[j] += fsrc;
         }
         float o[4];
-        const bool interior = (z >= M.pad) && (z < M.pad + M.nz) && (x >= M.pad) && (x + 3 < M.pad + M.nx);
+        interior[r] = (z >= M.pad) && (z < M.pad + M.nz) && (x >= M.pad) && (x + 3 < M.pad + M.nx);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float Fo = get(sv[r], j) * L[j];
-            D[r][j] = Fo * M.inv_dt2;
+            const float Fo = __fmul_rn(get(sv[r], j), L[j]);
+            D[r][j] = __fmul_rn(Fo, M.inv_dt2);
             float G = 1.f, am = 1.f;
-            if (!interior) {
-                const float e = sponge_e(M, z, x + j);
-                if (e != 0.f) {
-                    G = __frcp_rn(1.f + e);
-                    am = 1.f - e;
-                }
-            }
-            Gc[r][j] = G;
-            Am[r][j] = am;
-            o[j] = (full || x + j < M.Nx) ? G * (2.f * get(c, j) - am * get(uo[r], j) + Fo) : 0.f;
+            if (!interior[r]) sponge_factors(M, z, x + j, G, am);
+            o[j] = (full || x + j < M.Nx) ? leapfrog(G, get(c, j), am, get(uo[r], j), Fo) : 0.f;
         }
         if (valid[r]) {
             st4(ubase + po * F + off[r], make_float4(o[0], o[1], o[2], o[3]));
-            if (DTT)
+            if (DTT || (BORN && M.dtt_store))
                 st4(M.dtt + (long long)shot * M.dtt_shot_stride + (long long)M.dtt_slot * F + off[r],
                     make_float4(D[r][0], D[r][1], D[r][2], D[r][3]));
         }
@@ -244,12 +242,15 @@ __global__ void __launch_bounds__(kThreads) k_fwd2d(const __grid_constant__ Step
                 float4 c;
                 lap4<HX>(sf, lz + 16 * r + 4, lx + 4, M, c, L);
                 float o[4];
+                const int z = z0 + lz + 16 * r;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const float src = L[j] - get(dv[r], j) * D[r][j];
-                    o[j] = (full || x + j < M.Nx) ? Gc[r][j] * (2.f * get(c, j) - Am[r][j] * get(fo[r], j) +
-                                                                get(sv[r], j) * src)
-                                                  : 0.f;
+                    const float src = __fmaf_rn(-get(dv[r], j), D[r][j], L[j]);
+                    float G = 1.f, am = 1.f;
+                    if (!interior[r]) sponge_factors(M, z, x + j, G, am);
+                    o[j] = (full || x + j < M.Nx)
+                               ? leapfrog(G, get(c, j), am, get(fo[r], j), __fmul_rn(get(sv[r], j), src))
+                               : 0.f;
                 }
                 if (valid[r]) st4(fb + po * F + off[r], make_float4(o[0], o[1], o[2], o[3]));
             }
@@ -310,27 +311,14 @@ __global__ void __launch_bounds__(kThreads) k_adj2d(const __grid_constant__ Step
     const bool full = (x0 + kTX <= M.Nx);
     float4 sv[ROWS];
     long long off[ROWS];
-    bool valid[ROWS];
-    float Gc[ROWS][4], Am[ROWS][4];
+    bool valid[ROWS], interior[ROWS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
         const int z = z0 + lz + 16 * r;
         valid[r] = (z < M.Nz) && (x < M.Nx);
         off[r] = (long long)z * M.P + x;
         sv[r] = valid[r] ? ld4(M.s + off[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const bool interior = (z >= M.pad) && (z < M.pad + M.nz) && (x >= M.pad) && (x + 3 < M.pad + M.nx);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            Gc[r][j] = 1.f;
-            Am[r][j] = 1.f;
-            if (!interior) {
-                const float e = sponge_e(M, z, x + j);
-                if (e != 0.f) {
-                    Gc[r][j] = __frcp_rn(1.f + e);
-                    Am[r][j] = 1.f - e;
-                }
-            }
-        }
+        interior[r] = (z >= M.pad) && (z < M.pad + M.nz) && (x >= M.pad) && (x + 3 < M.pad + M.nx);
     }
 
     float acc[NBC][ROWS][4];
@@ -396,10 +384,12 @@ __global__ void __launch_bounds__(kThreads) k_adj2d(const __grid_constant__ Step
                         L[3] += iv.w;
                     }
                     float o[4];
+                    const int z = z0 + lz + 16 * r;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        o[j] = (full || x + j < M.Nx) ? Gc[r][j] * (2.f * get(c, j) - Am[r][j] * get(mo[r], j) +
-                                                                    get(sv[r], j) * L[j])
+                        float G = 1.f, am = 1.f;
+                        if (!interior[r]) sponge_factors(M, z, x + j, G, am);
+                        o[j] = (full || x + j < M.Nx) ? leapfrog(G, get(c, j), am, get(mo[r], j), __fmul_rn(get(sv[r], j), L[j]))
                                                       : 0.f;
                         acc[bi][r][j] = fmaf(-get(Dv[r], j), o[j], acc[bi][r][j]);
                     }

@@ -32,7 +32,7 @@ __device__ __forceinline__ float sponge_e3(const ModelStep3D& M, int z, int y, i
     const int rz = max(max(M.pad - z, z - (M.pad + M.nz - 1)), 0);
     const int ry = max(max(M.pad - y, y - (M.pad + M.ny - 1)), 0);
     const int rx = max(max(M.pad - x, x - (M.pad + M.nx - 1)), 0);
-    return M.cz * (float)(rz * rz) + M.cy * (float)(ry * ry) + M.cx * (float)(rx * rx);
+    return __fmaf_rn(M.cz, (float)(rz * rz), __fmaf_rn(M.cy, (float)(ry * ry), __fmul_rn(M.cx, (float)(rx * rx))));
 }
 
 template <int MODE, bool KAHAN>
@@ -168,10 +168,10 @@ __global__ void __launch_bounds__(kThreads) k_step3d(const __grid_constant__ Ste
             } else if (MODE == STEP3_BORN) {
                 const float4 dd = ld4(M.Din + (long long)shot * M.Din_shot_stride + off);
                 const float4 dmv = ld4(M.dm + (long long)b * F + off);
-                src[0] = -dmv.x * dd.x;
-                src[1] = -dmv.y * dd.y;
-                src[2] = -dmv.z * dd.z;
-                src[3] = -dmv.w * dd.w;
+                L[0] = __fmaf_rn(-dmv.x, dd.x, L[0]);  // Born source -dm Dtt u folded into L
+                L[1] = __fmaf_rn(-dmv.y, dd.y, L[1]);
+                L[2] = __fmaf_rn(-dmv.z, dd.z, L[2]);
+                L[3] = __fmaf_rn(-dmv.w, dd.w, L[3]);
             } else {
                 const float4 dd = ld4(M.Din + (long long)shot * M.Din_shot_stride + off);
                 Dv[0] = dd.x;
@@ -191,16 +191,10 @@ __global__ void __launch_bounds__(kThreads) k_step3d(const __grid_constant__ Ste
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float G = 1.f, am = 1.f;
-                if (!interior) {
-                    const float e = sponge_e3(M, z, y, x + j);
-                    if (e != 0.f) {
-                        G = __frcp_rn(1.f + e);
-                        am = 1.f - e;
-                    }
-                }
-                const float Fo = get(sv, j) * (L[j] + src[j]);
-                Dw[j] = Fo * M.inv_dt2;
-                o[j] = (x + j < M.Nx) ? G * (2.f * v[4 + j] - am * get(ov, j) + Fo) : 0.f;
+                if (!interior) sponge_pair(sponge_e3(M, z, y, x + j), G, am);
+                const float Fo = __fmul_rn(get(sv, j), __fadd_rn(L[j], src[j]));
+                Dw[j] = __fmul_rn(Fo, M.inv_dt2);
+                o[j] = (x + j < M.Nx) ? leapfrog(G, v[4 + j], am, get(ov, j), Fo) : 0.f;
             }
             st4(outv + off, make_float4(o[0], o[1], o[2], o[3]));
             if ((MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) && M.Dout)

@@ -35,15 +35,30 @@ def test_group_matches_individual_and_oracle(cuda_device):
            mini_config(3, shape=(57, 61), nt=220, ns=5, pad=6, p=2, model=1),
            mini_config(3, shape=(33, 70), nt=220, ns=2, pad=6, p=3, model=2)]
     probes = [make_probe(w) for w in wls]
+    for p in probes:      # fixed variants: the group and the solo runs sum in the same order
+        p.set_option("shot_group", 4)
+        p.set_option("pipeline", 2)
     dms = [torch.tensor(w.trials, device=cuda_device) for w in wls]
     outs = apply_H_group(probes, dms)
     for w, p, d, o in zip(wls, probes, dms, outs):
         solo = p.apply_H(d)
         assert torch.equal(o, solo)
     prob = problem_from_workload(wls[1])
+    refs = [prob.hessian(wls[1].trials[b].astype(np.float64)) for b in range(2)]
     for b in range(2):
-        ref = prob.hessian(wls[1].trials[b].astype(np.float64))
-        assert rel(outs[1][b].cpu().numpy(), ref) < 1e-4
+        assert rel(outs[1][b].cpu().numpy(), refs[b]) < 1e-4
+    # autotuned and graph-captured group (variants chosen by timing): same results up to
+    # the order of the image sums, twice in a row from the cached graph
+    tuned = [make_probe(w) for w in wls]
+    for p in tuned:
+        p.set_option("use_graph", 1)
+    first = apply_H_group(tuned, dms)
+    again = apply_H_group(tuned, dms)
+    for o, t, u in zip(outs, first, again):
+        assert torch.equal(t, u)
+        assert rel(t.cpu().numpy(), o.cpu().numpy()) < 1e-6
+    for b in range(2):
+        assert rel(first[1][b].cpu().numpy(), refs[b]) < 1e-4
 
 
 def test_group_rejects_mismatched_time_axes(cuda_device):

@@ -59,10 +59,12 @@ def test_migration_config1(cuda_device, cfg1):
     assert rel(img, adj) < 2e-5
 
 
-@pytest.mark.parametrize("snap,tol", [("fp32", 1e-4), ("bf16", 2e-3), ("fp16", 2e-3)])
+@pytest.mark.parametrize("snap,tol", [("fp32", 1e-4), ("bf16", 2e-3), ("fp16", 2e-3), ("history", 1e-4)])
 def test_hessian_config1(cuda_device, cfg1, snap, tol):
     wl, prob, born, r, adj, hes = cfg1
-    p = make_probe(wl, snapshot_dtype=snap)
+    p = make_probe(wl, snapshot_dtype="fp32" if snap == "history" else snap)
+    if snap == "history":
+        p.set_option("dtt_history", 1)          # Dtt u^n of every step kept, no recomputation
     hd = p.apply_H(dev(wl.trials)).cpu().numpy()[0]
     assert rel(hd, hes) < tol
 
@@ -107,6 +109,14 @@ def ragged():
     {"shot_group": 1},
     {"shot_group": 3, "tile_z": 32},
     {"shot_wave": 3, "shot_group": 2},
+    {"pipeline": 0},
+    {"pipeline": 3, "shot_group": 3},
+    {"pipeline": 3, "shot_wave": 2, "shot_group": 1},
+    {"pipeline": 4, "shot_group": 2},
+    {"dtt_history": 1},
+    {"dtt_history": 1, "pipeline": 0, "shot_wave": 2},
+    {"use_graph": 1},
+    {"use_graph": 1, "shot_wave": 2, "dtt_history": 1},
 ])
 def test_hessian_ragged_grid_and_launch_shapes(cuda_device, ragged, opts):
     wl, ref = ragged
@@ -116,6 +126,8 @@ def test_hessian_ragged_grid_and_launch_shapes(cuda_device, ragged, opts):
     hd = p.apply_H(dev(wl.trials)).cpu().numpy()
     for b in range(3):
         assert rel(hd[b], ref[b]) < 1e-4, (opts, b)
+    again = p.apply_H(dev(wl.trials)).cpu().numpy()      # second call (a replayed graph if captured)
+    assert np.array_equal(again, hd)
 
 
 def test_hessian_without_kahan_and_host_buffers(cuda_device, ragged):
@@ -206,3 +218,16 @@ def test_config2_full_size_dot_and_hessian_consistency(cuda_device, cfg2):
     rhs = float(torch.sum(dm.double() * img.double()))
     assert abs(lhs - rhs) / lhs < 1e-5
     assert rel(hd.cpu().numpy(), img.cpu().numpy()) < 1e-5
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(cuda_device):
+    """A device wait that nothing satisfies ends by its time limit and is reported."""
+    from paper_1101_3615_gb300 import binding
+    wl = mini_config(1, shape=(24, 26), nt=60, ns=1, pad=4)
+    p = make_probe(wl)
+    st = binding.lib.probe_diag_wait_timeout(p.handle, 200, None)
+    assert st == -4                                               # PROBE_ERR_TIMEOUT
+    assert b"timed out" in binding.lib.probe_last_error(p.handle)
+    out = p.apply_H(dev(wl.trials)).cpu().numpy()                 # the context still works
+    ref = problem_from_workload(wl).hessian(wl.trials[0].astype(np.float64))
+    assert rel(out[0], ref) < 1e-4
