@@ -57,6 +57,9 @@ def parse():
                     help="run only F (fwd) or F* (adj) once after one warm-up call: the small "
                          "command used for ncu captures of one kernel")
     ap.add_argument("--shots", type=int, default=0, help="use only the first N shots (0 = all)")
+    ap.add_argument("--pipeline", type=int, default=-1,
+                    help="with --profile: 0 one tile per CTA, 2 or 3 pipelined kernels (-1: autotuned)")
+    ap.add_argument("--pipe-rows", type=int, default=0, help="with --pipeline 2/3: rows per thread (1 or 2)")
     return ap.parse_args()
 
 
@@ -71,7 +74,10 @@ def profile_run(a, wl):
     p = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet, snapshot_dtype=a.snapshot)
     p.set_option("check_finite", 0)
     p.set_option("tile_z", 16)
-    p.set_option("use_graph", 1)      # each shot wave's sweeps replayed as one CUDA graph
+    if a.pipeline >= 0:               # fixed kernel variant (no timing under the profiler)
+        p.set_option("pipeline", a.pipeline)
+        if a.pipe_rows:
+            p.set_option("pipe_rows", a.pipe_rows)
     dm = torch.tensor(wl.trials, device=dev)
     if a.profile == "fwd":
         run = lambda: p.apply_F(dm)
@@ -310,12 +316,15 @@ def main():
     dm = torch.tensor(wl.trials, device=dev)
     out = torch.empty_like(dm)
     stream = torch.cuda.current_stream(dev)
+    # the library records CUDA events around the forward sweep only (two per step: the
+    # dominant kernel's launch time) -- set before the warm-up, which autotunes and
+    # captures the graphs that the timed steps replay
+    p.set_option("timing", 2)
     for _ in range(a.warmup):
         p.apply_H(dm, out=out)
     torch.cuda.synchronize(dev)
 
-    # timed region: K steps, per-sweep CUDA events recorded by the library
-    p.set_option("timing", 1)
+    # timed region: K steps
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -324,19 +333,8 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    fwd_ms = fwd_b = rec_ms = adj_ms = adj_b = 0.0
-    launches = fwd_l = adj_l = 0
-    for _ in range(a.steps):
+    for _ in range(a.steps):      # queued back to back; the library's sweep events do not synchronise
         p.apply_H(dm, out=out)
-        s = p.stats()
-        fwd_ms += s["ms_forward"]
-        fwd_b += s["bytes_forward"]
-        fwd_l += s["launches_forward"]
-        rec_ms += s["ms_recompute"]
-        adj_ms += s["ms_adjoint"]
-        adj_b += s["bytes_adjoint"]
-        adj_l += s["launches_adjoint"]
-        launches += s["launches_total"]
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
@@ -345,12 +343,23 @@ def main():
     ms_step = ms_total / a.steps
     value = weak_scaling_value(cells_per_h, world, ms_step) / 1e9
     h_per_s = weak_scaling_value(wl.trials.shape[0], world, ms_step)
+    # forward-sweep CUDA-event time and launch counts of the last timed step (same stream)
     stats = p.stats()
+    fwd_ms, fwd_b, fwd_l = stats["ms_forward"], stats["bytes_forward"], stats["launches_forward"]
+    launches = stats["launches_total"] * a.steps
+    # breakdown pass (after the timed region): events around every sweep segment
+    p.set_option("timing", 1)
+    p.apply_H(dm, out=out)
+    sb = p.stats()
     p.set_option("timing", 0)
+    rec_ms = sb["ms_recompute"]
+    adj_ms, adj_b, adj_l = sb["ms_adjoint"], sb["bytes_adjoint"], sb["launches_adjoint"]
 
     peak, peak_kind = measured_peaks()
     fwd_launch_bytes = fwd_b / max(fwd_l, 1)
     fwd_launch_ms = fwd_ms / max(fwd_l, 1)
+    if fwd_ms <= 0 or adj_ms <= 0:
+        raise RuntimeError("per-sweep CUDA-event times missing from the library statistics")
     achieved = fwd_launch_bytes / (fwd_launch_ms * 1e-3) / 1e9
     adj_achieved = (adj_b / max(adj_l, 1)) / ((adj_ms / max(adj_l, 1)) * 1e-3) / 1e9
 
@@ -455,9 +464,12 @@ def main():
                      "bytes_per_launch": fwd_launch_bytes, "avg_launch_ms": fwd_launch_ms,
                      "peak_kind": f"{peak_kind} hbm_gbs (copy)"},
         "adjoint_roofline": {"achieved": adj_achieved, "frac": adj_achieved / peak,
+                             "how": "breakdown step after the timed region",
                              "kernel": adj_name + " (adjoint step + imaging)"},
-        "sweep_ms_per_step": {"forward": fwd_ms / a.steps, "recompute": rec_ms / a.steps,
-                              "adjoint": adj_ms / a.steps},
+        "sweep_ms_per_step": {"forward": fwd_ms, "recompute": rec_ms, "adjoint": adj_ms,
+                              "how": "forward: CUDA events around the sweep in the last timed step; "
+                                     "recompute / adjoint: events around every checkpoint segment in "
+                                     "one extra step after the timed region"},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,

@@ -109,15 +109,22 @@ typedef enum {
     PROBE_OPT_SHOT_WAVE = 2,     /* max shots resident at once; 0 (default) = memory planner */
     PROBE_OPT_SHOT_GROUP = 3,    /* shots per CTA in the adjoint sweep; 0 = autotuned */
     PROBE_OPT_USE_GRAPH = 4,     /* 1 (default): replay sweeps from a captured CUDA graph */
-    PROBE_OPT_TIMING = 5,        /* 1: record per-sweep CUDA-event timings (probe_get_stats) */
+    PROBE_OPT_TIMING = 5,        /* CUDA-event timings read by probe_get_stats (recorded on the call's
+                                    stream, also inside replayed graphs; no call synchronises):
+                                    1 = every sweep (forward, recompute, adjoint), 2 = the forward
+                                    sweep only (two events per shot wave); 0 = off */
     PROBE_OPT_TILE_Z = 6,        /* 2D tile height override (16 or 32); 0 = default */
-    PROBE_OPT_PIPELINE = 7,      /* 2D: 0 = one tile per CTA; 2, 3 or 4 = persistent warp-specialised
-                                    CTAs with a 2-, 3- or 4-stage TMA ring (tile height 16) */
+    PROBE_OPT_PIPELINE = 7,      /* 2D: 0 = one tile per CTA; 2 or 3 = persistent warp-specialised
+                                    CTAs with a 2- or 3-stage TMA ring (tiles 64 x 16R, see
+                                    PROBE_OPT_PIPE_ROWS), for the forward and the adjoint.  Every
+                                    variant gives the same bits. */
     PROBE_OPT_DTT_HISTORY = 8,   /* 2D: 1 = keep Dtt u^n of every step in device memory instead of
                                     checkpointing and recomputing (FP32, W (nt-1) planes); 0 (default) */
-    PROBE_OPT_AUTOTUNE = 9       /* 1 (default): on the first call for a shape, time the kernel variants
-                                    (forward pipeline depth, adjoint variant and shot group) and keep the
-                                    fastest; setting PROBE_OPT_PIPELINE or PROBE_OPT_SHOT_GROUP turns it off */
+    PROBE_OPT_AUTOTUNE = 9,      /* 1 (default): on the first call for a shape, time the 2D kernel variants
+                                    (forward and adjoint kernel, pipeline depth, rows per thread, shot group)
+                                    and keep the fastest; setting PROBE_OPT_PIPELINE, PROBE_OPT_PIPE_ROWS or
+                                    PROBE_OPT_SHOT_GROUP turns it off */
+    PROBE_OPT_PIPE_ROWS = 10     /* 2D pipelined kernels: rows per thread R, tile 64 x 16R (1 or 2) */
 } probe_option;
 
 /* Counters and timings of the last apply call (probe_get_stats). */
@@ -143,6 +150,7 @@ typedef struct {
     int pipeline_forward;        /* 2D forward kernel: 0 one tile per CTA, 2..4 pipeline stages */
     int pipeline_adjoint;        /* 2D adjoint kernel: same encoding */
     int dtt_history;             /* 1 when Dtt u^n of every step was kept instead of recomputed */
+    int pipeline_rows;           /* rows per thread of the pipelined kernels (0: not pipelined) */
 } probe_stats;
 
 /* Create a handle for one background model and acquisition geometry.

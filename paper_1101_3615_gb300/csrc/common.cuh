@@ -123,6 +123,29 @@ __device__ __forceinline__ float get(const float4& v, int j) {
     return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
 
+// Kahan-compensated s += v with running compensation c (explicit roundings).
+__device__ __forceinline__ void kahan1(float& s, float& c, float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+__device__ __forceinline__ void kahan4(float4& s, float4& c, float v0, float v1, float v2, float v3) {
+    kahan1(s.x, c.x, v0);
+    kahan1(s.y, c.y, v1);
+    kahan1(s.z, c.z, v2);
+    kahan1(s.w, c.w, v3);
+}
+
+// a[j] += v for a runtime lane j of a 4-element register array (j outside 0..3: no-op).
+// Written as an unrolled select so that the array stays in registers.
+__device__ __forceinline__ void add_lane(float a[4], int j, float v) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k == j) a[k] += v;
+}
+
 // 8th-order central second-derivative weights w0..w4 (standard Taylor-series coefficients).
 #define PROBE_W0 (-205.0 / 72.0)
 #define PROBE_W1 (8.0 / 5.0)

@@ -31,7 +31,10 @@ struct Workspace {
     float* s_tmp = nullptr;   // [F]
     int* src_wave = nullptr;  // [W][2] padded sources of the wave
     CUtensorMap tm_u, tm_f;
-    CUtensorMap tm_up, tm_fp, tm_dmp, tm_dtp;  // plain 64 x 16 boxes (pipelined kernels)
+    // pipelined kernels: halo and plain boxes for tiles of 64 x 16 map_rows
+    CUtensorMap tm_wu, tm_wf;
+    CUtensorMap tm_up, tm_fp, tm_dmp, tm_dtp;
+    int map_rows = 0;
     int tm_tile_z = 0;
     long long generation = 0;
 };
@@ -39,7 +42,7 @@ struct Workspace {
 // A captured sweep (forward + adjoint of one wave) and the key it was captured for.
 struct TunedEntry {
     std::vector<long long> key;  // kind, adjoint, then shots and trials of each model (and handles for groups)
-    int pipe_fwd = 2, pipe_adj = 2, group = 4;
+    int pipe_fwd = 2, pipe_adj = 2, group = 4, rows = 2;
 };
 
 struct GraphEntry {
@@ -79,6 +82,10 @@ struct probe_s {
     int* d_rec_tile_ptr = nullptr;
     int* d_rec_tile_idx = nullptr;
     int tile_z = 16, tiles_x = 0, tiles_y = 1, tiles_z = 0, ntiles = 0;
+    // receivers by pipelined-kernel tile (64 x 16R), R = 1, 2
+    int* d_wrec_ptr[3] = {nullptr, nullptr, nullptr};
+    int* d_wrec_idx[3] = {nullptr, nullptr, nullptr};
+    int ws_rows = 2;             // rows per thread R of the pipelined kernels
     int* d_err = nullptr;
     probe::Workspace ws;
     probe::DevBuf stage_in, stage_out;
@@ -91,6 +98,13 @@ struct probe_s {
     std::vector<probe::TunedEntry> tuned;  // autotuner results by workload key
     probe_stats stats{};
     std::vector<cudaEvent_t> events;
+    // PROBE_OPT_TIMING: each shot wave records its own events (base ev_base); the sums are
+    // formed when the statistics are read, after the end event, so no call synchronises
+    int ev_base = 0;
+    cudaEvent_t ev_end = nullptr;
+    struct {
+        int pending = 0, nwaves = 0, nev = 0, ckpt = 0, hist = 0;
+    } tp;
     probe::FitCache* fit = nullptr;  // FFT plans and buffers of probe_fit / probe_apply_precond
     // captured sweeps (PROBE_OPT_USE_GRAPH), replayed on gstream
     cudaStream_t gstream = nullptr;

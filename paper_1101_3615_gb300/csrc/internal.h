@@ -29,13 +29,20 @@ constexpr int kZC3D = 32;      // 3D planes marched by one CTA
 struct alignas(128) ModelStep2D {
     CUtensorMap tm_u;    // incident-field planes  [W*2][Nz][P], halo box (64+8) x (TZ+8)
     CUtensorMap tm_f;    // Born / adjoint planes  [W*nb*2][Nz][P], halo box
-    CUtensorMap tm_up;   // the same planes with a plain 64 x 16 box (pipelined kernels)
-    CUtensorMap tm_fp;
+    // pipelined kernels, tile 64 x 16R (R = ws_rows): halo boxes (64+8) x (16R+8) and plain boxes
+    CUtensorMap tm_wu;
+    CUtensorMap tm_wf;
+    CUtensorMap tm_up;   // incident planes, plain box
+    CUtensorMap tm_fp;   // Born / adjoint planes, plain box
     CUtensorMap tm_sp;   // s, one plane, plain box
     CUtensorMap tm_dmp;  // dm, nb planes, plain box
     CUtensorMap tm_dtp;  // Dtt segment buffer, W * dtt_slots planes, plain box
     int Nz, Nx, P, pad, nz, nx;
     int tiles_x, tiles_z, ntiles;
+    int ws_rows;                 // pipelined kernels: rows per thread R (tile height 16R)
+    int ws_tiles_z, ws_ntiles;   // their tile grid
+    const int* ws_rec_ptr;       // receivers by pipelined tile (CSR over ws_ntiles)
+    const int* ws_rec_idx;
     int block_begin;   // first grid.z index of this model in the launch
     int item_begin;    // pipelined kernels: first work item of this model
     int dtt_slots;     // Dtt planes per shot in the segment buffer
@@ -52,6 +59,7 @@ struct alignas(128) ModelStep2D {
     float c0;          // w0 (1/hz^2 + 1/hx^2)
     float lz[4], lx[4];  // w_k / h^2 per axis, k = 1..4
     float cxm[4];        // x taps in first-difference form: sum_{k>m} w_k / hx^2, m = 0..3
+    float czm[4];        // z taps in the same form (pipelined kernels): sum_{k>m} w_k / hz^2
     float inv_dt2;
     float vol_inv;     // 1 / (hz hx)
     long long F;       // floats per plane (Nz * P)
@@ -135,11 +143,12 @@ cudaError_t launch_fwd2d(FwdKind kind, int tile_z, const StepParams2D& p, int bl
 cudaError_t launch_adj2d(int tile_z, int nbc, bool kahan, const StepParams2D& p, int blocks,
                          int chunks, cudaStream_t st);
 size_t fwd2d_smem_bytes(FwdKind kind, int tile_z);
-// Pipelined persistent variants (stencil2d_pipe.cu), tile height kPipeTZ, `stages`-deep TMA ring.
+// Pipelined persistent variants (stencil2d_pipe.cu): tiles of 64 x 16R (R = m[].ws_rows, 1 or 2),
+// `stages`-deep TMA ring.  They need the handle's plain tile height kPipeTZ for its receiver lists.
 constexpr int kPipeTZ = 16;
 cudaError_t launch_fwd2d_pipe(FwdKind kind, int stages, const StepParams2D& p, cudaStream_t st);
 cudaError_t launch_adj2d_pipe(int nbc, bool kahan, int stages, const StepParams2D& p, int chunks, cudaStream_t st);
-size_t pipe_smem_bytes(int stages, bool adjoint);
+size_t pipe_smem_bytes(int stages, bool adjoint, int rows);
 size_t adj2d_smem_bytes(int tile_z);
 cudaError_t stencil2d_configure();  // opt-in shared memory sizes
 

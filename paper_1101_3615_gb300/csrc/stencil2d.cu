@@ -45,11 +45,13 @@ __device__ __forceinline__ int find_model(const StepParams2D& p, int bz) {
 // The taps are accumulated from differences of neighbouring values, never from
 // the raw values against the centre term: those differences are nearly exact in
 // FP32, which removes the cancellation that otherwise dominates the round-off
-// of the time stepping for smooth, well-sampled fields.
-//   x: with d_i = v_{i+1} - v_i,  sum_k w_k (v_{c+k} + v_{c-k} - 2 v_c)
-//        = sum_{m=0..3} C_m (d_{c+m} - d_{c-m-1}),  C_m = sum_{k>m} w_k
-//      (11 shared differences for the thread's 4 cells);
-//   z: (v_{+k} - v) + (v_{-k} - v) per tap pair.
+// of the time stepping for smooth, well-sampled fields.  Per axis, with
+// d_i = v_{i+1} - v_i,
+//   sum_k w_k (v_{c+k} + v_{c-k} - 2 v_c) = sum_{m=0..3} C_m (d_{c+m} - d_{c-m-1}),
+//   C_m = sum_{k>m} w_k / h^2;
+// x first (11 shared differences for the thread's 4 cells), then z (8 per
+// column).  The pipelined kernels evaluate the same operations in the same
+// order, so both families give the same bits.
 template <int HX>
 __device__ __forceinline__ void lap4(const float* t, int row, int col, const ModelStep2D& M,
                                      float4& center, float L[4]) {
@@ -67,14 +69,18 @@ __device__ __forceinline__ void lap4(const float* t, int row, int col, const Mod
         for (int m = 1; m < 4; ++m) acc = fmaf(M.cxm[m], d[4 + j + m] - d[3 + j - m], acc);
         L[j] = acc;
     }
+    // z, outward from the centre row: the term m pairs d_{3-m} = v_{4-m} - v_{3-m} below
+    // with d_{4+m} = v_{5+m} - v_{4+m} above (v_4 = b), so few rows are live at once.
+    float4 lo = b, hi = b;
 #pragma unroll
-    for (int k = 1; k <= 4; ++k) {
-        const float4 up = ld4(rp - k * HX), dn = ld4(rp + k * HX);
-        const float w = M.lz[k - 1];
-        L[0] = fmaf(w, (up.x - b.x) + (dn.x - b.x), L[0]);
-        L[1] = fmaf(w, (up.y - b.y) + (dn.y - b.y), L[1]);
-        L[2] = fmaf(w, (up.z - b.z) + (dn.z - b.z), L[2]);
-        L[3] = fmaf(w, (up.w - b.w) + (dn.w - b.w), L[3]);
+    for (int m = 0; m < 4; ++m) {
+        const float4 dn = ld4(rp - (m + 1) * HX), up = ld4(rp + (m + 1) * HX);
+        L[0] = fmaf(M.czm[m], (up.x - hi.x) - (lo.x - dn.x), L[0]);
+        L[1] = fmaf(M.czm[m], (up.y - hi.y) - (lo.y - dn.y), L[1]);
+        L[2] = fmaf(M.czm[m], (up.z - hi.z) - (lo.z - dn.z), L[2]);
+        L[3] = fmaf(M.czm[m], (up.w - hi.w) - (lo.w - dn.w), L[3]);
+        lo = dn;
+        hi = up;
     }
 }
 
@@ -113,7 +119,7 @@ __device__ __forceinline__ void abort_cta(int* err, uint64_t* bars, int nbars,
 }
 
 template <int TZ, int KIND>
-__global__ void __launch_bounds__(kThreads) k_fwd2d(const __grid_constant__ StepParams2D p) {
+__global__ void __launch_bounds__(kThreads, TZ == 16 ? 4 : 3) k_fwd2d(const __grid_constant__ StepParams2D p) {
     using T = Tile2D<TZ>;
     constexpr int HX = T::HX;
     constexpr int ROWS = T::ROWS;
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd2d(const __grid_constant__ Step
         lap4<HX>(su, lz + 16 * r + 4, lx + 4, M, c, L);
         if (z == sz) {
             const int j = sx - x;
-            if (j >= 0 && j < 4) L[j] += fsrc;
+            add_lane(L, j, fsrc);
         }
         float o[4];
         interior[r] = (z >= M.pad) && (z < M.pad + M.nz) && (x >= M.pad) && (x + 3 < M.pad + M.nx);
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd2d(const __grid_constant__ Step
 }
 
 template <int TZ, int NBC, bool KAHAN>
-__global__ void __launch_bounds__(kThreads) k_adj2d(const __grid_constant__ StepParams2D p) {
+__global__ void __launch_bounds__(kThreads, (NBC * TZ <= 32) ? 4 : 2) k_adj2d(const __grid_constant__ StepParams2D p) {
     using T = Tile2D<TZ>;
     constexpr int HX = T::HX;
     constexpr int ROWS = T::ROWS;
@@ -414,15 +420,7 @@ __global__ void __launch_bounds__(kThreads) k_adj2d(const __grid_constant__ Step
                 if (KAHAN) {
                     float* cp = cmp + boff + off[r];
                     float4 cv = ld4(cp);
-                    float* ia = reinterpret_cast<float*>(&iv);
-                    float* ca = reinterpret_cast<float*>(&cv);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float y = acc[bi][r][j] - ca[j];
-                        const float t = ia[j] + y;
-                        ca[j] = (t - ia[j]) - y;
-                        ia[j] = t;
-                    }
+                    kahan4(iv, cv, acc[bi][r][0], acc[bi][r][1], acc[bi][r][2], acc[bi][r][3]);
                     st4(cp, cv);
                 } else {
                     iv.x += acc[bi][r][0];

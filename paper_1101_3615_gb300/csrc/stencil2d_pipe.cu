@@ -2,20 +2,28 @@
 //
 // The plain kernels of stencil2d.cu give every CTA one tile (load, wait,
 // compute, store), so each CTA exposes the full load latency.  Here a
-// persistent CTA walks a list of work groups -- one field of one 64 x 16 tile:
-// the incident field, one Born field, or one adjoint field of one shot -- with
+// persistent CTA walks a list of work groups -- one field of one 64 x 16R
+// tile: the incident field, one Born field, or one adjoint field of one shot --
+// with
 //   * one producer warp that decodes the next group, writes its descriptor to
 //     shared memory and issues its TMA loads into an S-stage ring: the radius-4
-//     halo tile of the differentiated field (72 x 24) and up to three plain
-//     64 x 16 tiles of pointwise operands (previous level, s, dm, Dtt); for
-//     adjoint tiles that hold receivers it also assembles the injection tile;
+//     halo tile of the differentiated field ((64+8) x (16R+8)) and plain
+//     64 x 16R tiles of the pointwise operands (previous level, s, dm, Dtt);
+//     for adjoint tiles that hold receivers it also assembles the injection tile;
 //   * eight consumer warps that wait on the stage's "full" mbarrier, compute,
 //     store from registers, and release the stage through its "empty"
 //     mbarrier (one arrival per warp).
+// Each consumer thread owns R consecutive rows of 4 cells, so the z taps share
+// their first differences across the rows (the same first-difference form as
+// the x taps) and the per-group bookkeeping is spread over 4R cells.  Operands
+// shared by the groups of one work item stay in registers: s and Dtt u^n of the
+// incident step for the Born fields; s for all adjoint groups of an item and
+// Dtt for all trials of one shot.  Tiles whose cells are all interior take a
+// path without sponge or edge logic.
 // There is no CTA-wide barrier in the main loop; a sentinel descriptor ends
 // the list.  Every wait is bounded (2 s of %globaltimer) and reports through
-// the device error word.  Arithmetic, boundary handling and the adjoint form
-// are those of stencil2d.cu.
+// the device error word.  The arithmetic is that of stencil2d.cu operation for
+// operation, so both kernel families give the same bits.
 #include "common.cuh"
 #include "internal.h"
 
@@ -23,22 +31,28 @@ namespace probe {
 
 namespace {
 
-constexpr int TZ = kPipeTZ;
 constexpr int HX = kTX + 8;
-constexpr int HZ = TZ + 8;
-constexpr int HALO = HX * HZ;   // floats
-constexpr int PLAIN = kTX * TZ; // floats
-constexpr int FWD_STAGE = HALO + 2 * PLAIN;
-constexpr int ADJ_STAGE = HALO + 4 * PLAIN;  // + injection tile
-constexpr unsigned HALO_B = HALO * 4u, PLAIN_B = PLAIN * 4u;
-constexpr int kConsumerWarps = kThreads / 32;     // 8
-constexpr int kWsThreads = kThreads + 32;        // + producer warp
+constexpr int kConsumerWarps = kThreads / 32;  // 8
+constexpr int kWsThreads = kThreads + 32;      // + producer warp
+
+template <int R>
+struct Ws {
+    static constexpr int TZ = 16 * R;
+    static constexpr int HZ = TZ + 8;
+    static constexpr int HALO = HX * HZ;    // floats
+    static constexpr int PLAIN = kTX * TZ;  // floats
+    static constexpr int FWD_STAGE = HALO + 2 * PLAIN;
+    static constexpr int ADJ_STAGE = HALO + 4 * PLAIN;  // mu^{n+2}, Dtt, s, injection tile
+    static constexpr unsigned HALO_B = HALO * 4u, PLAIN_B = PLAIN * 4u;
+};
 
 struct Group {
     int mi, unit, tile, x0, z0;
-    int f;      // forward: field (0 incident, 1.. Born trial + 1); adjoint: shot-in-group * NBC + trial-in-chunk
-    int last;   // adjoint: last group of its item
+    int f;      // forward: field (0 incident, 1.. Born trial + 1); adjoint: shot-in-group * NBC + trial-in-chunk;
+                // -1 ends the list
+    int last;   // adjoint: the group's last shot (the trial's image update happens here)
     int inj;    // adjoint: injection tile present
+    int fast;   // every cell of the tile is an interior cell (no sponge, no grid edge)
     int sz, sx; // forward: source cell of the shot
     int rbeg, rend;  // receivers of the tile (CSR range)
     float fsrc; // forward: w[n] / (hz hx)
@@ -52,61 +66,127 @@ __device__ __forceinline__ int model_of(const StepParams2D& p, int item) {
     return mi;
 }
 
-__device__ __forceinline__ void sponge_fac(const ModelStep2D& M, int z, int x, float& G, float& am) {
-    const int rz = max(max(M.pad - z, z - (M.pad + M.nz - 1)), 0);
-    const int rx = max(max(M.pad - x, x - (M.pad + M.nx - 1)), 0);
-    sponge_pair(__fmaf_rn(M.cz, (float)(rz * rz), __fmul_rn(M.cx, (float)(rx * rx))), G, am);
+// One cell of the time update; rhs = s (L + source) of the field.  Interior
+// ("fast") tiles have G = a- = 1; elsewhere the sponge factors follow from the
+// cell's distance to the interior, and columns past Nx are written as zero.
+__device__ __forceinline__ float cell_update(const ModelStep2D& M, bool fast, int z, int x, float c, float prev,
+                                             float rhs) {
+    float G = 1.f, am = 1.f;
+    if (!fast) {
+        if (x >= M.Nx) return 0.f;
+        const int rz = max(max(M.pad - z, z - (M.pad + M.nz - 1)), 0);
+        const int rx = max(max(M.pad - x, x - (M.pad + M.nx - 1)), 0);
+        sponge_pair(__fmaf_rn(M.cz, (float)(rz * rz), __fmul_rn(M.cx, (float)(rx * rx))), G, am);
+    }
+    return leapfrog(G, c, am, prev, rhs);
 }
 
-// Laplacian of 4 cells at halo-tile coordinates (row, col); first-difference x taps.
-__device__ __forceinline__ void lap4p(const float* t, int row, int col, const ModelStep2D& M, float4& center,
-                                      float L[4]) {
+// Laplacian of R rows x 4 cells whose first cell sits at halo coordinates (row, col).
+// Both axes in first-difference form: with d_i = v_{i+1} - v_i,
+//   sum_k w_k (v_{c+k} + v_{c-k} - 2 v_c) = sum_{m=0..3} C_m (d_{c+m} - d_{c-m-1}),
+//   C_m = sum_{k>m} w_k / h^2,
+// x first (11 shared differences per row), then z (R + 7 shared differences per column).
+template <int R>
+__device__ __forceinline__ void lap_rows(const float* t, int row, int col, const ModelStep2D& M, float4 c[R],
+                                         float L[R][4]) {
     const float* rp = t + row * HX + col;
-    const float4 a = ld4(rp - 4), b = ld4(rp), c = ld4(rp + 4);
-    const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-    center = b;
-    float d[11];
 #pragma unroll
-    for (int i = 0; i < 11; ++i) d[i] = v[i + 1] - v[i];
+    for (int r = 0; r < R; ++r) {
+        const float4 a = ld4(rp + r * HX - 4), b = ld4(rp + r * HX), e = ld4(rp + r * HX + 4);
+        c[r] = b;
+        const float w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, e.x, e.y, e.z, e.w};
+        float d[11];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        float acc = M.cxm[0] * (d[4 + j] - d[3 + j]);
+        for (int i = 0; i < 11; ++i) d[i] = w[i + 1] - w[i];
 #pragma unroll
-        for (int m = 1; m < 4; ++m) acc = fmaf(M.cxm[m], d[4 + j + m] - d[3 + j - m], acc);
-        L[j] = acc;
+        for (int j = 0; j < 4; ++j) {
+            float acc = M.cxm[0] * (d[4 + j] - d[3 + j]);
+#pragma unroll
+            for (int m = 1; m < 4; ++m) acc = fmaf(M.cxm[m], d[4 + j + m] - d[3 + j - m], acc);
+            L[r][j] = acc;
+        }
     }
+    // z, outward: rows below the first cell row (lo) and above the last (hi) are loaded
+    // as the tap index m grows; row r's term m is C_m ((v_{r+m+1} - v_{r+m}) - (v_{r-m} - v_{r-m-1})).
+    // Differences between rows inside the block are formed once and shared by the R rows.
+    if (R == 1) {
+        float4 lo = c[0], hi = c[0];
 #pragma unroll
-    for (int k = 1; k <= 4; ++k) {
-        const float4 up = ld4(rp - k * HX), dn = ld4(rp + k * HX);
-        const float w = M.lz[k - 1];
-        L[0] = fmaf(w, (up.x - b.x) + (dn.x - b.x), L[0]);
-        L[1] = fmaf(w, (up.y - b.y) + (dn.y - b.y), L[1]);
-        L[2] = fmaf(w, (up.z - b.z) + (dn.z - b.z), L[2]);
-        L[3] = fmaf(w, (up.w - b.w) + (dn.w - b.w), L[3]);
+        for (int m = 0; m < 4; ++m) {
+            const float4 dn = ld4(rp - (m + 1) * HX), up = ld4(rp + (m + 1) * HX);
+            L[0][0] = fmaf(M.czm[m], (up.x - hi.x) - (lo.x - dn.x), L[0][0]);
+            L[0][1] = fmaf(M.czm[m], (up.y - hi.y) - (lo.y - dn.y), L[0][1]);
+            L[0][2] = fmaf(M.czm[m], (up.z - hi.z) - (lo.z - dn.z), L[0][2]);
+            L[0][3] = fmaf(M.czm[m], (up.w - hi.w) - (lo.w - dn.w), L[0][3]);
+            lo = dn;
+            hi = up;
+        }
+    } else {
+        // R = 2: values v_{-4..5} relative to row 0; g_i = v_{i+1} - v_i.
+        // row 0 term m: g_m - g_{-m-1}; row 1 term m: g_{m+1} - g_{-m}.
+        const float4 c0 = c[0], c1 = c[1];
+        float4 gin = make_float4(c1.x - c0.x, c1.y - c0.y, c1.z - c0.z, c1.w - c0.w);  // g_0
+        float4 lo = c0, hi = c1;        // current outermost rows below / above
+        float4 glo = gin, ghi = gin;    // g_{-m} (row 1's lower) and g_m (row 0's upper) of the last step
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float4 dn = ld4(rp - (m + 1) * HX), up = ld4(rp + (m + 2) * HX);
+            const float4 gd = make_float4(lo.x - dn.x, lo.y - dn.y, lo.z - dn.z, lo.w - dn.w);  // g_{-m-1}
+            const float4 gu = make_float4(up.x - hi.x, up.y - hi.y, up.z - hi.z, up.w - hi.w);  // g_{m+1}
+            L[0][0] = fmaf(M.czm[m], ghi.x - gd.x, L[0][0]);
+            L[0][1] = fmaf(M.czm[m], ghi.y - gd.y, L[0][1]);
+            L[0][2] = fmaf(M.czm[m], ghi.z - gd.z, L[0][2]);
+            L[0][3] = fmaf(M.czm[m], ghi.w - gd.w, L[0][3]);
+            L[R - 1][0] = fmaf(M.czm[m], gu.x - glo.x, L[R - 1][0]);
+            L[R - 1][1] = fmaf(M.czm[m], gu.y - glo.y, L[R - 1][1]);
+            L[R - 1][2] = fmaf(M.czm[m], gu.z - glo.z, L[R - 1][2]);
+            L[R - 1][3] = fmaf(M.czm[m], gu.w - glo.w, L[R - 1][3]);
+            lo = dn;
+            hi = up;
+            glo = gd;
+            ghi = gu;
+        }
     }
 }
 
+template <int R>
 __device__ __forceinline__ Group decode(const StepParams2D& p, int item) {
     Group q;
     q.mi = model_of(p, item);
     const ModelStep2D& M = p.m[q.mi];
     const int r = item - M.item_begin;
-    q.unit = r / M.ntiles;
-    q.tile = r - q.unit * M.ntiles;
+    q.unit = r / M.ws_ntiles;
+    q.tile = r - q.unit * M.ws_ntiles;
     const int tz = q.tile / M.tiles_x;
-    q.z0 = tz * TZ;
+    q.z0 = tz * Ws<R>::TZ;
     q.x0 = (q.tile - tz * M.tiles_x) * kTX;
     q.f = 0;
     q.last = 0;
     q.inj = 0;
+    q.fast = (q.z0 >= M.pad) && (q.z0 + Ws<R>::TZ <= M.pad + M.nz) && (q.x0 >= M.pad) &&
+             (q.x0 + kTX <= M.pad + M.nx);
+    q.rbeg = M.ws_rec_ptr[q.tile];
+    q.rend = M.ws_rec_ptr[q.tile + 1];
+    q.sz = q.sx = 0;
+    q.fsrc = 0.f;
     return q;
 }
 
 __device__ __forceinline__ void fail_exit(int* err) { set_dev_error(err, DEVERR_TIMEOUT); }
 
+// Receivers of the tile sampled from a staged halo tile (field at time n).
+__device__ __forceinline__ void sample_recv(const float* st, const ModelStep2D& M, const Group& q, float* out,
+                                            int tid) {
+    for (int i = q.rbeg + tid; i < q.rend; i += kThreads) {
+        const int r = M.ws_rec_idx[i];
+        out[r] = st[(M.rec_zx[2 * r] - q.z0 + 4) * HX + (M.rec_zx[2 * r + 1] - q.x0 + 4)];
+    }
+}
+
 // ---- forward ---------------------------------------------------------------
-template <int KIND, int S, bool MULTI>
-__global__ void __launch_bounds__(kWsThreads) k_fwd2d_ws(const __grid_constant__ StepParams2D p) {
+template <int KIND, int S, bool MULTI, int R>
+__global__ void __launch_bounds__(kWsThreads, R == 1 ? 4 : 3) k_fwd2d_ws(const __grid_constant__ StepParams2D p) {
+    using T = Ws<R>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ Group info[S];
@@ -125,14 +205,14 @@ __global__ void __launch_bounds__(kWsThreads) k_fwd2d_ws(const __grid_constant__
 
     if (warp == kConsumerWarps) {  // ---------------- producer warp
         if (lane != 0) return;
-        int g = 0;
+        int s = 0, g = 0;
+        uint32_t eph = 0;  // phase of empty[s] to wait for (once the ring has wrapped)
         for (int item = blockIdx.x;; item += gridDim.x) {
             const bool done = item >= total;
-            Group q = done ? Group{} : decode(p, item);
+            Group q = done ? Group{} : decode<R>(p, item);
             const int ngr = done ? 1 : (KIND == FWD_BORN ? 1 + p.m[q.mi].nb : 1);
             for (int f = 0; f < ngr; ++f, ++g) {
-                const int s = g % S;
-                if (g >= S && !mbar_wait_bounded(&empty[s], (uint32_t)(((g / S) - 1) & 1))) {
+                if (g >= S && !mbar_wait_bounded(&empty[s], eph)) {
                     fail_exit(p.err);
                     return;
                 }
@@ -147,113 +227,118 @@ __global__ void __launch_bounds__(kWsThreads) k_fwd2d_ws(const __grid_constant__
                     q.sz = M.src_zx[2 * q.unit];
                     q.sx = M.src_zx[2 * q.unit + 1];
                     q.fsrc = M.wavelet[n] * M.vol_inv;
-                    q.rbeg = M.rec_tile_ptr[q.tile];
-                    q.rend = M.rec_tile_ptr[q.tile + 1];
                 }  // later fields of the same item keep these values
                 info[s] = q;
-                float* st = smem + s * FWD_STAGE;
-                mbar_expect_tx(&full[s], HALO_B + 2 * PLAIN_B);
+                float* st = smem + s * T::FWD_STAGE;
+                mbar_expect_tx(&full[s], T::HALO_B + 2 * T::PLAIN_B);
                 if (f == 0) {
-                    tma_load_3d(st, &M.tm_u, q.x0 - 4, q.z0 - 4, q.unit * 2 + pc, &full[s]);
-                    tma_load_3d(st + HALO, &M.tm_sp, q.x0, q.z0, 0, &full[s]);
-                    tma_load_3d(st + HALO + PLAIN, &M.tm_up, q.x0, q.z0, q.unit * 2 + po, &full[s]);
+                    tma_load_3d(st, &M.tm_wu, q.x0 - 4, q.z0 - 4, q.unit * 2 + pc, &full[s]);
+                    tma_load_3d(st + T::HALO, &M.tm_sp, q.x0, q.z0, 0, &full[s]);
+                    tma_load_3d(st + T::HALO + T::PLAIN, &M.tm_up, q.x0, q.z0, q.unit * 2 + po, &full[s]);
                 } else {
                     const int b = f - 1;
                     const int pl = (q.unit * M.nb + b) * 2;
-                    tma_load_3d(st, &M.tm_f, q.x0 - 4, q.z0 - 4, pl + pc, &full[s]);
-                    tma_load_3d(st + HALO, &M.tm_dmp, q.x0, q.z0, b, &full[s]);
-                    tma_load_3d(st + HALO + PLAIN, &M.tm_fp, q.x0, q.z0, pl + po, &full[s]);
+                    tma_load_3d(st, &M.tm_wf, q.x0 - 4, q.z0 - 4, pl + pc, &full[s]);
+                    tma_load_3d(st + T::HALO, &M.tm_dmp, q.x0, q.z0, b, &full[s]);
+                    tma_load_3d(st + T::HALO + T::PLAIN, &M.tm_fp, q.x0, q.z0, pl + po, &full[s]);
+                }
+                if (++s == S) {
+                    s = 0;
+                    if (g + 1 >= 2 * S) eph ^= 1u;  // the wait for group g+1 is for use (g+1)/S - 1
                 }
             }
         }
     }
 
     // ---------------- consumer warps
-    const int lx = (tid & 15) << 2, lz = tid >> 4;
-    float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
-    float D[4] = {0.f, 0.f, 0.f, 0.f};
-    bool interior = false;
-    for (int g = 0;; ++g) {
-        const int s = g % S;
-        if (!mbar_wait_bounded(&full[s], (uint32_t)((g / S) & 1))) {
+    const int lx = (tid & 15) << 2, lz = (tid >> 4) * R;
+    float4 sv[R];
+    float D[R][4];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        sv[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) D[r][j] = 0.f;
+    }
+    int s = 0;
+    uint32_t ph = 0;
+    for (;;) {
+        if (!mbar_wait_bounded(&full[s], ph)) {
             fail_exit(p.err);
             return;
         }
         const Group q = info[s];
         if (q.f < 0) return;
         const ModelStep2D& M = p.m[MULTI ? q.mi : 0];  // single model: loop-invariant descriptor
-        const float* st = smem + s * FWD_STAGE;
+        const float* st = smem + s * T::FWD_STAGE;
         const int shot = q.unit;
-        const int x = q.x0 + lx, z = q.z0 + lz;
-        const bool valid = (z < M.Nz) && (x < M.Nx);
-        const bool full_w = (q.x0 + kTX <= M.Nx);
-        const long long off = (long long)z * M.P + x;
-        float L[4];
-        float4 c;
-        lap4p(st, lz + 4, lx + 4, M, c, L);
-        const float4 pa = ld4(st + HALO + lz * kTX + lx);
-        const float4 pold = ld4(st + HALO + PLAIN + lz * kTX + lx);
-        float o[4];
+        const int x = q.x0 + lx;
+        const bool fast = q.fast != 0;
+        float L[R][4];
+        float4 c[R];
+        lap_rows<R>(st, lz + 4, lx + 4, M, c, L);
         if (q.f == 0) {
-            interior = (z >= M.pad) && (z < M.pad + M.nz) && (x >= M.pad) && (x + 3 < M.pad + M.nx);
-            sv = pa;
-            if (z == q.sz) {
-                const int j = q.sx - x;
-                if (j >= 0 && j < 4) L[j] += q.fsrc;
-            }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float Fo = __fmul_rn(get(sv, j), L[j]);
-                D[j] = __fmul_rn(Fo, M.inv_dt2);
-                float G = 1.f, am = 1.f;
-                if (!interior) sponge_fac(M, z, x + j, G, am);
-                o[j] = (full_w || x + j < M.Nx) ? leapfrog(G, get(c, j), am, get(pold, j), Fo) : 0.f;
-            }
-            if (valid) {
-                st4(M.u + (long long)(shot * 2 + po) * M.F + off, make_float4(o[0], o[1], o[2], o[3]));
-                if (KIND == FWD_INCIDENT_DTT || (KIND == FWD_BORN && M.dtt_store))
-                    st4(M.dtt + (long long)shot * M.dtt_shot_stride + (long long)M.dtt_slot * M.F + off,
-                        make_float4(D[0], D[1], D[2], D[3]));
-            }
-            if (KIND == FWD_INCIDENT_SAMPLE && q.rend > q.rbeg) {
-                const int beg = q.rbeg, end = q.rend;
-                float* out = M.data + (long long)shot * M.data_shot_stride + (long long)n * M.nr;
-                for (int i = beg + tid; i < end; i += kThreads) {
-                    const int r = M.rec_tile_idx[i];
-                    out[r] = st[(M.rec_zx[2 * r] - q.z0 + 4) * HX + (M.rec_zx[2 * r + 1] - q.x0 + 4)];
+            for (int r = 0; r < R; ++r) {
+                const int z = q.z0 + lz + r;
+                sv[r] = ld4(st + T::HALO + (lz + r) * kTX + lx);
+                const float4 pold = ld4(st + T::HALO + T::PLAIN + (lz + r) * kTX + lx);
+                if (z == q.sz) add_lane(L[r], q.sx - x, q.fsrc);
+                float o[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float Fo = __fmul_rn(get(sv[r], j), L[r][j]);
+                    D[r][j] = __fmul_rn(Fo, M.inv_dt2);
+                    o[j] = cell_update(M, fast, z, x + j, get(c[r], j), get(pold, j), Fo);
+                }
+                if (fast || (z < M.Nz && x < M.Nx)) {
+                    const long long off = (long long)z * M.P + x;
+                    st4(M.u + (long long)(shot * 2 + po) * M.F + off, make_float4(o[0], o[1], o[2], o[3]));
+                    if (KIND == FWD_INCIDENT_DTT || (KIND == FWD_BORN && M.dtt_store))
+                        st4(M.dtt + (long long)shot * M.dtt_shot_stride + (long long)M.dtt_slot * M.F + off,
+                            make_float4(D[r][0], D[r][1], D[r][2], D[r][3]));
                 }
             }
+            if (KIND == FWD_INCIDENT_SAMPLE && q.rend > q.rbeg)
+                sample_recv(st, M, q, M.data + (long long)shot * M.data_shot_stride + (long long)n * M.nr, tid);
         } else {
             const int b = q.f - 1;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float G = 1.f, am = 1.f;
-                if (!interior) sponge_fac(M, z, x + j, G, am);
-                const float src = __fmaf_rn(-get(pa, j), D[j], L[j]);
-                o[j] = (full_w || x + j < M.Nx) ? leapfrog(G, get(c, j), am, get(pold, j), __fmul_rn(get(sv, j), src))
-                                                : 0.f;
-            }
-            if (valid)
-                st4(M.f + (long long)((shot * M.nb + b) * 2 + po) * M.F + off, make_float4(o[0], o[1], o[2], o[3]));
-            const int beg = q.rbeg, end = q.rend;
-            if (end > beg) {
-                float* out = M.data + (long long)shot * M.data_shot_stride + (long long)b * M.data_trial_stride +
-                             (long long)n * M.nr;
-                for (int i = beg + tid; i < end; i += kThreads) {
-                    const int r = M.rec_tile_idx[i];
-                    out[r] = st[(M.rec_zx[2 * r] - q.z0 + 4) * HX + (M.rec_zx[2 * r + 1] - q.x0 + 4)];
+            for (int r = 0; r < R; ++r) {
+                const int z = q.z0 + lz + r;
+                const float4 dmv = ld4(st + T::HALO + (lz + r) * kTX + lx);
+                const float4 fo = ld4(st + T::HALO + T::PLAIN + (lz + r) * kTX + lx);
+                float o[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float src = __fmaf_rn(-get(dmv, j), D[r][j], L[r][j]);
+                    o[j] = cell_update(M, fast, z, x + j, get(c[r], j), get(fo, j), __fmul_rn(get(sv[r], j), src));
                 }
+                if (fast || (z < M.Nz && x < M.Nx))
+                    st4(M.f + (long long)((shot * M.nb + b) * 2 + po) * M.F + (long long)z * M.P + x,
+                        make_float4(o[0], o[1], o[2], o[3]));
             }
+            if (q.rend > q.rbeg)
+                sample_recv(st, M, q,
+                            M.data + (long long)shot * M.data_shot_stride + (long long)b * M.data_trial_stride +
+                                (long long)n * M.nr,
+                            tid);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+        }
     }
 }
 
 // ---- adjoint ---------------------------------------------------------------
-// Item = (model, shot group, tile); its groups are (shot jj of the group, trial bi of the chunk).
-template <int NBC, bool KAHAN, int S, bool MULTI>
-__global__ void __launch_bounds__(kWsThreads) k_adj2d_ws(const __grid_constant__ StepParams2D p) {
+// Item = (model, shot group, tile); its groups are (shot jj of the group, trial bi of the chunk),
+// jj-major.  s is staged with the item's first group, Dtt with each shot's first trial.
+template <int NBC, bool KAHAN, int S, bool MULTI, int R>
+__global__ void __launch_bounds__(kWsThreads, (NBC * R >= 8) ? 1 : 2) k_adj2d_ws(const __grid_constant__ StepParams2D p) {
+    using T = Ws<R>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ Group info[S];
@@ -271,10 +356,11 @@ __global__ void __launch_bounds__(kWsThreads) k_adj2d_ws(const __grid_constant__
     __syncthreads();
 
     if (warp == kConsumerWarps) {  // ---------------- producer warp
-        int g = 0;
+        int s = 0, g = 0;
+        uint32_t eph = 0;
         for (int item = blockIdx.x;; item += gridDim.x) {
             const bool done = item >= total;
-            Group q = done ? Group{} : decode(p, item);
+            Group q = done ? Group{} : decode<R>(p, item);
             int nsh = 1, nbc = 1;
             if (!done) {
                 const ModelStep2D& M = p.m[q.mi];
@@ -283,9 +369,8 @@ __global__ void __launch_bounds__(kWsThreads) k_adj2d_ws(const __grid_constant__
             }
             for (int jj = 0; jj < nsh; ++jj) {
                 for (int bi = 0; bi < nbc; ++bi, ++g) {
-                    const int s = g % S;
                     bool ok = true;
-                    if (lane == 0 && g >= S) ok = mbar_wait_bounded(&empty[s], (uint32_t)(((g / S) - 1) & 1));
+                    if (lane == 0 && g >= S) ok = mbar_wait_bounded(&empty[s], eph);
                     if (!__shfl_sync(0xffffffffu, ok, 0)) {
                         if (lane == 0) fail_exit(p.err);
                         return;
@@ -298,19 +383,18 @@ __global__ void __launch_bounds__(kWsThreads) k_adj2d_ws(const __grid_constant__
                         return;
                     }
                     const ModelStep2D& M = p.m[q.mi];
-                    float* st = smem + s * ADJ_STAGE;
+                    float* st = smem + s * T::ADJ_STAGE;
                     const int shot = q.unit * M.shot_group + jj;
                     const int b = M.chunk * NBC + bi;
-                    const int rbeg = M.rec_tile_ptr[q.tile], rend = M.rec_tile_ptr[q.tile + 1];
-                    const bool inj = rend > rbeg;
+                    const bool inj = q.rend > q.rbeg;
                     if (inj) {  // R^T r^n of this tile, assembled by the producer warp
-                        float* it = st + HALO + 3 * PLAIN;
-                        for (int i = lane; i < PLAIN; i += 32) it[i] = 0.f;
+                        float* it = st + T::HALO + 3 * T::PLAIN;
+                        for (int i = lane; i < T::PLAIN / 4; i += 32) st4(it + 4 * i, make_float4(0.f, 0.f, 0.f, 0.f));
                         __syncwarp();
                         const float* rr = M.rdata + (long long)shot * M.data_shot_stride +
                                           (long long)b * M.data_trial_stride + (long long)n * M.nr;
-                        for (int i = rbeg + lane; i < rend; i += 32) {
-                            const int rcv = M.rec_tile_idx[i];
+                        for (int i = q.rbeg + lane; i < q.rend; i += 32) {
+                            const int rcv = M.ws_rec_idx[i];
                             atomicAdd(&it[(M.rec_zx[2 * rcv] - q.z0) * kTX + (M.rec_zx[2 * rcv + 1] - q.x0)], rr[rcv]);
                         }
                         __syncwarp();
@@ -318,112 +402,128 @@ __global__ void __launch_bounds__(kWsThreads) k_adj2d_ws(const __grid_constant__
                     if (lane == 0) {
                         Group gi = q;
                         gi.f = jj * NBC + bi;
-                        gi.last = (jj == nsh - 1) && (bi == nbc - 1);
+                        gi.last = jj == nsh - 1;  // trial bi's sum over the shot group is complete here
                         gi.inj = inj;
                         info[s] = gi;
                         const int pl = (shot * M.nb + b) * 2;
-                        mbar_expect_tx(&full[s], HALO_B + 3 * PLAIN_B);
-                        tma_load_3d(st, &M.tm_f, q.x0 - 4, q.z0 - 4, pl + pc, &full[s]);
-                        tma_load_3d(st + HALO, &M.tm_fp, q.x0, q.z0, pl + po, &full[s]);
-                        tma_load_3d(st + HALO + PLAIN, &M.tm_dtp, q.x0, q.z0, shot * M.dtt_slots + M.dtt_slot,
-                                    &full[s]);
-                        tma_load_3d(st + HALO + 2 * PLAIN, &M.tm_sp, q.x0, q.z0, 0, &full[s]);
+                        const bool with_d = bi == 0, with_s = (jj == 0) && (bi == 0);
+                        mbar_expect_tx(&full[s], T::HALO_B + T::PLAIN_B + (with_d ? T::PLAIN_B : 0u) +
+                                                     (with_s ? T::PLAIN_B : 0u));
+                        tma_load_3d(st, &M.tm_wf, q.x0 - 4, q.z0 - 4, pl + pc, &full[s]);
+                        tma_load_3d(st + T::HALO, &M.tm_fp, q.x0, q.z0, pl + po, &full[s]);
+                        if (with_d)
+                            tma_load_3d(st + T::HALO + T::PLAIN, &M.tm_dtp, q.x0, q.z0,
+                                        shot * M.dtt_slots + M.dtt_slot, &full[s]);
+                        if (with_s) tma_load_3d(st + T::HALO + 2 * T::PLAIN, &M.tm_sp, q.x0, q.z0, 0, &full[s]);
                     }
                     __syncwarp();
+                    if (++s == S) {
+                        s = 0;
+                        if (g + 1 >= 2 * S) eph ^= 1u;  // the wait for group g+1 is for use (g+1)/S - 1
+                    }
                 }
             }
         }
     }
 
     // ---------------- consumer warps
-    const int lx = (tid & 15) << 2, lz = tid >> 4;
-    float acc[NBC][4];
+    const int lx = (tid & 15) << 2, lz = (tid >> 4) * R;
+    float acc[NBC][R][4];
 #pragma unroll
     for (int k = 0; k < NBC; ++k)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[k][j] = 0.f;
-    for (int g = 0;; ++g) {
-        const int s = g % S;
-        if (!mbar_wait_bounded(&full[s], (uint32_t)((g / S) & 1))) {
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[k][r][j] = 0.f;
+    float4 sv[R], Dv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) sv[r] = Dv[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int s = 0;
+    uint32_t ph = 0;
+    for (;;) {
+        if (!mbar_wait_bounded(&full[s], ph)) {
             fail_exit(p.err);
             return;
         }
         const Group q = info[s];
         if (q.f < 0) return;
         const ModelStep2D& M = p.m[MULTI ? q.mi : 0];  // single model: loop-invariant descriptor
-        const float* st = smem + s * ADJ_STAGE;
+        const float* st = smem + s * T::ADJ_STAGE;
         const int jj = q.f / NBC, bi = q.f - (q.f / NBC) * NBC;
         const int shot = q.unit * M.shot_group + jj;
         const int b = M.chunk * NBC + bi;
-        const int x = q.x0 + lx, z = q.z0 + lz;
-        const bool valid = (z < M.Nz) && (x < M.Nx);
-        const bool full_w = (q.x0 + kTX <= M.Nx);
-        const bool interior = (z >= M.pad) && (z < M.pad + M.nz) && (x >= M.pad) && (x + 3 < M.pad + M.nx);
-        const long long off = (long long)z * M.P + x;
-        float L[4];
-        float4 c;
-        lap4p(st, lz + 4, lx + 4, M, c, L);
-        const float4 mo = ld4(st + HALO + lz * kTX + lx);
-        const float4 Dv = ld4(st + HALO + PLAIN + lz * kTX + lx);
-        const float4 sv = ld4(st + HALO + 2 * PLAIN + lz * kTX + lx);
-        if (q.inj) {
-            const float4 iv = ld4(st + HALO + 3 * PLAIN + lz * kTX + lx);
-            L[0] += iv.x;
-            L[1] += iv.y;
-            L[2] += iv.z;
-            L[3] += iv.w;
+        const int x = q.x0 + lx;
+        const bool fast = q.fast != 0;
+        if (bi == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) Dv[r] = ld4(st + T::HALO + T::PLAIN + (lz + r) * kTX + lx);
         }
-        float o[4];
+        if (q.f == 0) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float G = 1.f, am = 1.f;
-            if (!interior) sponge_fac(M, z, x + j, G, am);
-            o[j] = (full_w || x + j < M.Nx) ? leapfrog(G, get(c, j), am, get(mo, j), __fmul_rn(get(sv, j), L[j]))
-                                            : 0.f;
+            for (int r = 0; r < R; ++r) sv[r] = ld4(st + T::HALO + 2 * T::PLAIN + (lz + r) * kTX + lx);
         }
+        float L[R][4];
+        float4 c[R];
+        lap_rows<R>(st, lz + 4, lx + 4, M, c, L);
 #pragma unroll
-        for (int k = 0; k < NBC; ++k)
-            if (k == bi) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[k][j] = fmaf(-get(Dv, j), o[j], acc[k][j]);
+        for (int r = 0; r < R; ++r) {
+            const int z = q.z0 + lz + r;
+            const float4 mo = ld4(st + T::HALO + (lz + r) * kTX + lx);
+            if (q.inj) {
+                const float4 in = ld4(st + T::HALO + 3 * T::PLAIN + (lz + r) * kTX + lx);
+                L[r][0] += in.x;
+                L[r][1] += in.y;
+                L[r][2] += in.z;
+                L[r][3] += in.w;
             }
-        if (valid) st4(M.f + (long long)((shot * M.nb + b) * 2 + po) * M.F + off, make_float4(o[0], o[1], o[2], o[3]));
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-        if (q.last) {  // image update of this item's shot group
-            const int nbc = min(NBC, M.nb - M.chunk * NBC);
-            if (valid) {
-                float* img = M.img + (long long)q.unit * M.img_group_stride;
-                float* cmp = M.comp + (long long)q.unit * M.img_group_stride;
+            float o[4];
 #pragma unroll
-                for (int k = 0; k < NBC; ++k) {
-                    if (k < nbc) {
-                        const long long boff = (long long)(M.chunk * NBC + k) * M.F + off;
-                        float4 iv = ld4(img + boff);
-                        float* ia = reinterpret_cast<float*>(&iv);
-                        if (KAHAN) {
-                            float4 cv = ld4(cmp + boff);
-                            float* ca = reinterpret_cast<float*>(&cv);
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const float y = acc[k][j] - ca[j];
-                                const float t = ia[j] + y;
-                                ca[j] = (t - ia[j]) - y;
-                                ia[j] = t;
-                            }
-                            st4(cmp + boff, cv);
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) ia[j] += acc[k][j];
-                        }
-                        st4(img + boff, iv);
-                    }
-                }
-            }
+            for (int j = 0; j < 4; ++j)
+                o[j] = cell_update(M, fast, z, x + j, get(c[r], j), get(mo, j), __fmul_rn(get(sv[r], j), L[r][j]));
 #pragma unroll
             for (int k = 0; k < NBC; ++k)
+                if (k == bi) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[k][j] = 0.f;
+                    for (int j = 0; j < 4; ++j) acc[k][r][j] = fmaf(-get(Dv[r], j), o[j], acc[k][r][j]);
+                }
+            if (fast || (z < M.Nz && x < M.Nx))
+                st4(M.f + (long long)((shot * M.nb + b) * 2 + po) * M.F + (long long)z * M.P + x,
+                    make_float4(o[0], o[1], o[2], o[3]));
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+        }
+        if (q.last) {  // trial b's sum over the shot group is complete: add it to its image
+            float* img = M.img + (long long)q.unit * M.img_group_stride + (long long)b * M.F;
+            float* cmp = M.comp + (long long)q.unit * M.img_group_stride + (long long)b * M.F;
+#pragma unroll
+            for (int k = 0; k < NBC; ++k)
+                if (k == bi) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int z = q.z0 + lz + r;
+                        if (fast || (z < M.Nz && x < M.Nx)) {
+                            const long long off = (long long)z * M.P + x;
+                            float4 iv = ld4(img + off);
+                            if (KAHAN) {
+                                float4 cv = ld4(cmp + off);
+                                kahan4(iv, cv, acc[k][r][0], acc[k][r][1], acc[k][r][2], acc[k][r][3]);
+                                st4(cmp + off, cv);
+                            } else {
+                                iv.x += acc[k][r][0];
+                                iv.y += acc[k][r][1];
+                                iv.z += acc[k][r][2];
+                                iv.w += acc[k][r][3];
+                            }
+                            st4(img + off, iv);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[k][r][j] = 0.f;
+                    }
+                }
         }
     }
 }
@@ -456,69 +556,80 @@ cudaError_t launch_persistent(K kernel, size_t smem, int total, const StepParams
     return cudaGetLastError();
 }
 
-}  // namespace
-
-size_t pipe_smem_bytes(int stages, bool adjoint) {
-    return (size_t)stages * (adjoint ? ADJ_STAGE : FWD_STAGE) * 4;
+template <int R>
+size_t smem_bytes(int stages, bool adjoint) {
+    return (size_t)stages * (adjoint ? Ws<R>::ADJ_STAGE : Ws<R>::FWD_STAGE) * 4;
 }
 
-cudaError_t launch_fwd2d_pipe(FwdKind kind, int stages, const StepParams2D& p, cudaStream_t st) {
+template <int K, int R>
+cudaError_t launch_fwd_kr(int stages, const StepParams2D& p, cudaStream_t st) {
+    const size_t sm = smem_bytes<R>(stages, false);
     const int total = p.total_items;
-    if (total <= 0) return cudaSuccess;
-    const size_t sm = pipe_smem_bytes(stages, false);
-#define PROBE_FWD_CASE(K)                                                                            \
-    case K:                                                                                          \
-        if (p.nmodels > 1)                                                                           \
-            return stages == 4   ? launch_persistent(k_fwd2d_ws<K, 4, true>, sm, total, p, st)       \
-                   : stages == 3 ? launch_persistent(k_fwd2d_ws<K, 3, true>, sm, total, p, st)       \
-                                 : launch_persistent(k_fwd2d_ws<K, 2, true>, sm, total, p, st);      \
-        return stages == 4   ? launch_persistent(k_fwd2d_ws<K, 4, false>, sm, total, p, st)          \
-               : stages == 3 ? launch_persistent(k_fwd2d_ws<K, 3, false>, sm, total, p, st)          \
-                             : launch_persistent(k_fwd2d_ws<K, 2, false>, sm, total, p, st);
+    if (p.nmodels > 1)
+        return stages == 3 ? launch_persistent(k_fwd2d_ws<K, 3, true, R>, sm, total, p, st)
+                           : launch_persistent(k_fwd2d_ws<K, 2, true, R>, sm, total, p, st);
+    return stages == 3 ? launch_persistent(k_fwd2d_ws<K, 3, false, R>, sm, total, p, st)
+                       : launch_persistent(k_fwd2d_ws<K, 2, false, R>, sm, total, p, st);
+}
+
+template <int NB, bool KH, int R>
+cudaError_t launch_adj_nkr(int stages, const StepParams2D& q, cudaStream_t st) {
+    const size_t sm = smem_bytes<R>(stages, true);
+    const int total = q.total_items;
+    if (q.nmodels > 1)
+        return stages == 3 ? launch_persistent(k_adj2d_ws<NB, KH, 3, true, R>, sm, total, q, st)
+                           : launch_persistent(k_adj2d_ws<NB, KH, 2, true, R>, sm, total, q, st);
+    return stages == 3 ? launch_persistent(k_adj2d_ws<NB, KH, 3, false, R>, sm, total, q, st)
+                       : launch_persistent(k_adj2d_ws<NB, KH, 2, false, R>, sm, total, q, st);
+}
+
+template <int NB, bool KH>
+cudaError_t launch_adj_nk(int stages, const StepParams2D& q, cudaStream_t st) {
+    return q.m[0].ws_rows == 2 ? launch_adj_nkr<NB, KH, 2>(stages, q, st) : launch_adj_nkr<NB, KH, 1>(stages, q, st);
+}
+
+}  // namespace
+
+size_t pipe_smem_bytes(int stages, bool adjoint, int rows) {
+    return rows == 2 ? smem_bytes<2>(stages, adjoint) : smem_bytes<1>(stages, adjoint);
+}
+
+// stages: 2 or 3 (anything else runs 2); the tile height is 16 * p.m[0].ws_rows (same for all models).
+cudaError_t launch_fwd2d_pipe(FwdKind kind, int stages, const StepParams2D& p, cudaStream_t st) {
+    if (p.total_items <= 0) return cudaSuccess;
+    const bool r2 = p.m[0].ws_rows == 2;
     switch (kind) {
-        PROBE_FWD_CASE(FWD_INCIDENT)
-        PROBE_FWD_CASE(FWD_INCIDENT_DTT)
-        PROBE_FWD_CASE(FWD_BORN)
-        PROBE_FWD_CASE(FWD_INCIDENT_SAMPLE)
+        case FWD_INCIDENT:
+            return r2 ? launch_fwd_kr<FWD_INCIDENT, 2>(stages, p, st) : launch_fwd_kr<FWD_INCIDENT, 1>(stages, p, st);
+        case FWD_INCIDENT_DTT:
+            return r2 ? launch_fwd_kr<FWD_INCIDENT_DTT, 2>(stages, p, st)
+                      : launch_fwd_kr<FWD_INCIDENT_DTT, 1>(stages, p, st);
+        case FWD_BORN:
+            return r2 ? launch_fwd_kr<FWD_BORN, 2>(stages, p, st) : launch_fwd_kr<FWD_BORN, 1>(stages, p, st);
+        case FWD_INCIDENT_SAMPLE:
+            return r2 ? launch_fwd_kr<FWD_INCIDENT_SAMPLE, 2>(stages, p, st)
+                      : launch_fwd_kr<FWD_INCIDENT_SAMPLE, 1>(stages, p, st);
     }
-#undef PROBE_FWD_CASE
     return cudaErrorInvalidValue;
 }
 
+// nbc: trials per CTA (1, 2, 4 or 8; at most 4 with two rows per thread).
 cudaError_t launch_adj2d_pipe(int nbc, bool kahan, int stages, const StepParams2D& p, int chunks, cudaStream_t st) {
-    const int total = p.total_items;
-    if (total <= 0) return cudaSuccess;
-    const size_t sm = pipe_smem_bytes(stages, true);
+    if (p.total_items <= 0) return cudaSuccess;
+    if (nbc == 8 && p.m[0].ws_rows == 2) return cudaErrorInvalidValue;
     StepParams2D q = p;
     for (int c = 0; c < chunks; ++c) {
         for (int k = 0; k < q.nmodels; ++k) q.m[k].chunk = c;
         cudaError_t e;
-#define PROBE_ADJ_SM(NB, KH, MU)                                                            \
-    e = stages == 4   ? launch_persistent(k_adj2d_ws<NB, KH, 4, MU>, sm, total, q, st)      \
-        : stages == 3 ? launch_persistent(k_adj2d_ws<NB, KH, 3, MU>, sm, total, q, st)      \
-                      : launch_persistent(k_adj2d_ws<NB, KH, 2, MU>, sm, total, q, st);
-#define PROBE_ADJ_S(NB, KH)            \
-    if (q.nmodels > 1) {               \
-        PROBE_ADJ_SM(NB, KH, true)     \
-    } else {                           \
-        PROBE_ADJ_SM(NB, KH, false)    \
-    }
-#define PROBE_ADJ(NB)           \
-    if (kahan) {                \
-        PROBE_ADJ_S(NB, true)   \
-    } else {                    \
-        PROBE_ADJ_S(NB, false)  \
-    }
         switch (nbc) {
-            case 1: PROBE_ADJ(1) break;
-            case 2: PROBE_ADJ(2) break;
-            case 4: PROBE_ADJ(4) break;
-            case 8: PROBE_ADJ(8) break;
+            case 1: e = kahan ? launch_adj_nk<1, true>(stages, q, st) : launch_adj_nk<1, false>(stages, q, st); break;
+            case 2: e = kahan ? launch_adj_nk<2, true>(stages, q, st) : launch_adj_nk<2, false>(stages, q, st); break;
+            case 4: e = kahan ? launch_adj_nk<4, true>(stages, q, st) : launch_adj_nk<4, false>(stages, q, st); break;
+            case 8:
+                e = kahan ? launch_adj_nkr<8, true, 1>(stages, q, st) : launch_adj_nkr<8, false, 1>(stages, q, st);
+                break;
             default: return cudaErrorInvalidValue;
         }
-#undef PROBE_ADJ
-#undef PROBE_ADJ_S
-#undef PROBE_ADJ_SM
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_step3d(const __grid_constant__ Ste
             if (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) {
                 if (z == sz && y == sy) {
                     const int j = sx - x;
-                    if (j >= 0 && j < 4) src[j] = fsrc;
+                    add_lane(src, j, fsrc);
                 }
             } else if (MODE == STEP3_BORN) {
                 const float4 dd = ld4(M.Din + (long long)shot * M.Din_shot_stride + off);
@@ -202,22 +202,18 @@ __global__ void __launch_bounds__(kThreads) k_step3d(const __grid_constant__ Ste
             if (MODE == STEP3_ADJ) {
                 float* ip = M.img + (long long)(shot * M.nfield + b) * F + off;
                 float4 iv = ld4(ip);
-                float* ivp = reinterpret_cast<float*>(&iv);
+                const float t0 = __fmul_rn(-Dv[0], o[0]), t1 = __fmul_rn(-Dv[1], o[1]);
+                const float t2 = __fmul_rn(-Dv[2], o[2]), t3 = __fmul_rn(-Dv[3], o[3]);
                 if (KAHAN) {
                     float* cp = M.comp + (long long)(shot * M.nfield + b) * F + off;
                     float4 cv = ld4(cp);
-                    float* cvp = reinterpret_cast<float*>(&cv);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float yv = -Dv[j] * o[j] - cvp[j];
-                        const float tv = ivp[j] + yv;
-                        cvp[j] = (tv - ivp[j]) - yv;
-                        ivp[j] = tv;
-                    }
+                    kahan4(iv, cv, t0, t1, t2, t3);
                     st4(cp, cv);
                 } else {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) ivp[j] = fmaf(-Dv[j], o[j], ivp[j]);
+                    iv.x = __fadd_rn(iv.x, t0);
+                    iv.y = __fadd_rn(iv.y, t1);
+                    iv.z = __fadd_rn(iv.z, t2);
+                    iv.w = __fadd_rn(iv.w, t3);
                 }
                 st4(ip, iv);
             }

@@ -112,7 +112,9 @@ def ragged():
     {"pipeline": 0},
     {"pipeline": 3, "shot_group": 3},
     {"pipeline": 3, "shot_wave": 2, "shot_group": 1},
-    {"pipeline": 4, "shot_group": 2},
+    {"pipeline": 2, "pipe_rows": 1, "shot_group": 2},
+    {"pipeline": 3, "pipe_rows": 2, "shot_wave": 3},
+    {"pipe_rows": 2, "shot_wave": 2, "shot_group": 1, "dtt_history": 1},
     {"dtt_history": 1},
     {"dtt_history": 1, "pipeline": 0, "shot_wave": 2},
     {"use_graph": 1},
@@ -128,6 +130,52 @@ def test_hessian_ragged_grid_and_launch_shapes(cuda_device, ragged, opts):
         assert rel(hd[b], ref[b]) < 1e-4, (opts, b)
     again = p.apply_H(dev(wl.trials)).cpu().numpy()      # second call (a replayed graph if captured)
     assert np.array_equal(again, hd)
+
+
+def test_kernel_variants_give_identical_bits(cuda_device, ragged):
+    """Every 2D kernel family and tile shape, and the Dtt history, evaluate the same
+    operations in the same order: F, F* and H agree bit for bit (same shot grouping)."""
+    wl, _ = ragged
+    y = dev(wl.trials)
+    d0 = None
+    outs = []
+    for opts in [{"pipeline": 0}, {"pipeline": 2, "pipe_rows": 1}, {"pipeline": 3, "pipe_rows": 2},
+                 {"pipeline": 2, "pipe_rows": 2, "use_graph": 1}, {"pipeline": 3, "pipe_rows": 1, "dtt_history": 1}]:
+        p = make_probe(wl)
+        p.set_option("shot_group", 2)
+        for k, v in opts.items():
+            p.set_option(k, v)
+        d = p.apply_F(y)
+        if d0 is None:
+            d0 = d
+        assert torch.equal(d, d0), opts
+        outs.append((opts, p.apply_Fadj(d0), p.apply_H(y)))
+    for opts, img, hy in outs[1:]:
+        assert torch.equal(img, outs[0][1]), opts
+        assert torch.equal(hy, outs[0][2]), opts
+
+
+@pytest.mark.parametrize("opts", [{}, {"use_graph": 1}, {"use_graph": 1, "dtt_history": 1}])
+def test_sweep_timing_events(cuda_device, ragged, opts):
+    """PROBE_OPT_TIMING: per-sweep CUDA-event times (also from inside a replayed graph),
+    formed when the statistics are read; the timed call's result is unchanged."""
+    wl, ref = ragged
+    p = make_probe(wl)
+    for k, v in opts.items():
+        p.set_option(k, v)
+    y = dev(wl.trials)
+    h0 = p.apply_H(y)
+    p.set_option("timing", 1)
+    for _ in range(2):
+        h1 = p.apply_H(y)
+    s = p.stats()
+    assert torch.equal(h0, h1)
+    assert s["ms_forward"] > 0 and s["ms_adjoint"] > 0
+    if opts.get("dtt_history"):
+        assert s["ms_recompute"] == 0 and s["dtt_history"] == 1
+    else:
+        assert s["ms_recompute"] > 0
+    assert abs(s["ms_total"] - (s["ms_forward"] + s["ms_recompute"] + s["ms_adjoint"])) < 1e-6
 
 
 def test_hessian_without_kahan_and_host_buffers(cuda_device, ragged):
