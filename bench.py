@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--pipeline", type=int, default=-1,
                     help="with --profile: 0 one tile per CTA, 2 or 3 pipelined kernels (-1: autotuned)")
     ap.add_argument("--pipe-rows", type=int, default=0, help="with --pipeline 2/3: rows per thread (1 or 2)")
+    ap.add_argument("--fixed", default="",
+                    help="pf,pa,R,G: fixed forward / adjoint kernel variants, rows per thread and shots "
+                         "per adjoint CTA instead of the autotuner (for runs under a profiler)")
     return ap.parse_args()
 
 
@@ -206,14 +209,17 @@ def kernel_label(pipeline, adjoint):
     return name, "stencil2d.cu"
 
 
-def ncu_traffic(kind, source):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel source."""
+def ncu_traffic(kind, source, variant):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel
+    source and variant (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d[kind]
         if e.get("source") != source or e.get("source_sha") != kernel_source_hash(source):
+            return None
+        if any(variant.get(k) != v for k, v in e.get("variant", {}).items()):
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:
@@ -313,6 +319,10 @@ def main():
     p.set_option("check_finite", 0)
     p.set_option("tile_z", 16)
     p.set_option("use_graph", 1)      # each shot wave's sweeps replayed as one CUDA graph
+    if a.fixed:
+        pf, pa, rows, grp = (int(v) for v in a.fixed.split(","))
+        for k, v in (("pipeline", pf), ("pipeline_adj", pa), ("pipe_rows", rows), ("shot_group", grp)):
+            p.set_option(k, v)
     dm = torch.tensor(wl.trials, device=dev)
     out = torch.empty_like(dm)
     stream = torch.cuda.current_stream(dev)
@@ -439,7 +449,8 @@ def main():
 
     fwd_name, fwd_src = kernel_label(stats["pipeline_forward"], False)
     adj_name, adj_src = kernel_label(stats["pipeline_adjoint"], True)
-    traffic = ncu_traffic("fwd_born", fwd_src)
+    traffic = ncu_traffic("fwd_born", fwd_src, {"pipeline_forward": stats["pipeline_forward"],
+                                                "pipeline_rows": stats["pipeline_rows"]})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -451,7 +462,7 @@ def main():
                    "shot_wave": stats["shot_wave"], "shot_group": stats["shot_group"],
                    "tile_z": stats["tile_z"], "pipeline_forward": stats["pipeline_forward"],
                    "pipeline_adjoint": stats["pipeline_adjoint"], "cuda_graph": True,
-                   "autotuned": True,
+                   "autotuned": not a.fixed,
                    "l2": f"inputs larger than L2: {wl.ns} shots x 4 field planes x "
                          f"{wl.cells_padded() * 4 / 1e6:.2f} MB = "
                          f"{wl.ns * 4 * wl.cells_padded() * 4 / 1e6:.0f} MB live state per step "

@@ -124,7 +124,8 @@ typedef enum {
                                     (forward and adjoint kernel, pipeline depth, rows per thread, shot group)
                                     and keep the fastest; setting PROBE_OPT_PIPELINE, PROBE_OPT_PIPE_ROWS or
                                     PROBE_OPT_SHOT_GROUP turns it off */
-    PROBE_OPT_PIPE_ROWS = 10     /* 2D pipelined kernels: rows per thread R, tile 64 x 16R (1 or 2) */
+    PROBE_OPT_PIPE_ROWS = 10,    /* 2D pipelined kernels: rows per thread R, tile 64 x 16R (1 or 2) */
+    PROBE_OPT_PIPELINE_ADJ = 11  /* 2D adjoint kernel only (0, 2 or 3; PROBE_OPT_PIPELINE sets both) */
 } probe_option;
 
 /* Counters and timings of the last apply call (probe_get_stats). */

@@ -21,7 +21,7 @@ STATUS = {0: "PROBE_OK", -1: "PROBE_ERR_ARG", -2: "PROBE_ERR_CUDA", -3: "PROBE_E
           -4: "PROBE_ERR_TIMEOUT", -5: "PROBE_ERR_NONFINITE", -6: "PROBE_ERR_STATE"}
 SNAP = {"fp32": 0, "bf16": 1, "fp16": 2}
 OPT = {"check_finite": 1, "shot_wave": 2, "shot_group": 3, "use_graph": 4, "timing": 5, "tile_z": 6,
-       "pipeline": 7, "dtt_history": 8, "autotune": 9, "pipe_rows": 10}
+       "pipeline": 7, "dtt_history": 8, "autotune": 9, "pipe_rows": 10, "pipeline_adj": 11}
 
 
 class probe_grid(C.Structure):

@@ -1074,6 +1074,11 @@ extern "C" probe_status probe_set_option(probe_t h, int key, long long v) {
         case PROBE_OPT_AUTOTUNE:
             h->opt_autotune = v ? 1 : 0;
             return PROBE_OK;
+        case PROBE_OPT_PIPELINE_ADJ:
+            if (v != 0 && v != 2 && v != 3) return fail(h, PROBE_ERR_ARG, "adjoint pipeline must be 0, 2 or 3");
+            h->pipe_adj = (int)v;
+            h->user_fixed = 1;
+            return PROBE_OK;
         case PROBE_OPT_PIPE_ROWS:
             if (v != 1 && v != 2) return fail(h, PROBE_ERR_ARG, "pipelined rows per thread must be 1 or 2");
             h->ws_rows = (int)v;
