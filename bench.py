@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-history", action="store_true",
                     help="skip the extra measurement with the full Dtt history resident")
-    ap.add_argument("--snapshot", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--snapshot", default="fp16", choices=["fp32", "bf16", "fp16"],
+                    help="checkpoint storage of the batched path (default: FP16 with per-plane scale)")
     ap.add_argument("--profile", default=None, choices=["fwd", "adj"],
                     help="run only F (fwd) or F* (adj) once after one warm-up call: the small "
                          "command used for ncu captures of one kernel")
@@ -135,7 +136,7 @@ def oracle_sample(cfg, nshots, nt_sample):
 class ClockSampler:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,clocks.mem")
 
     def __init__(self, index):
         self.index = index
@@ -165,7 +166,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, mem, pw = [], None, set(), [], []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -174,13 +175,18 @@ class ClockSampler:
             try:
                 sm.append(float(f[1]))
                 mx = float(f[2])
+                pw.append(float(f[3]))
+                if len(f) > 9:
+                    mem.append(float(f[9]))
             except ValueError:
                 continue
             for nm, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "mem_mhz": statistics.median(mem) if mem else None,
+                "power_w_median": statistics.median(pw) if pw else None}
 
 
 def measured_peaks():
@@ -254,7 +260,13 @@ def main():
         wl.src = wl.src[:a.shots]
     if a.profile:
         return profile_run(a, wl)
-    cells_per_h = 4.0 * wl.cells_padded() * (wl.nt - 1) * wl.ns * wl.trials.shape[0]
+    # executed cell-updates per H application over all trials: the batched path runs u0 and its
+    # recompute once per shot and a Born and an adjoint field per (shot, trial): 2 + 2p sweeps;
+    # the plain per-(shot, trial) path runs all four sweeps for every trial: 4p
+    ntr = wl.trials.shape[0]
+    sweep_cells = float(wl.cells_padded()) * (wl.nt - 1) * wl.ns
+    cells_per_h = (2 + 2 * ntr) * sweep_cells
+    cells_plain = 4 * ntr * sweep_cells
 
     if a.impl == "reference":
         if rank != 0:
@@ -387,13 +399,16 @@ def main():
     e2e = {"value": cells_per_h * world / e2e_s / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": int(dm_host.nbytes), "d2h_bytes_per_step": int(out_host.nbytes)}
 
-    # quick FP32 dot-product test on the full workload (stated error)
-    d = p.apply_F(dm)
-    img = p.apply_Fadj(d)
+    # FP32 dot-product test on the full workload (stated error): FP32 checkpoints, with which
+    # F* is the transpose of F to round-off (16-bit checkpoints perturb Dtt u^n)
+    p32 = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet, snapshot_dtype="fp32")
+    p32.set_option("check_finite", 0)
+    d = p32.apply_F(dm)
+    img = p32.apply_Fadj(d)
     lhs = float(torch.sum(d.double() ** 2))
     rhs = float(torch.sum(dm.double() * img.double()))
     dot_err = abs(lhs - rhs) / abs(lhs)
-    del d, img
+    del d, img, p32
 
     # same step with Dtt u^n of every time step kept in HBM (no checkpoint recompute)
     hist = None
@@ -414,7 +429,9 @@ def main():
             eh1.record(stream)
             torch.cuda.synchronize(dev)
             hms = max_over_ranks(eh0.elapsed_time(eh1) / nh)
-            hist = {"value": weak_scaling_value(cells_per_h, world, hms) / 1e9, "unit": UNIT,
+            # executed cell-updates: no recompute sweep (u0 + trials x (Born + adjoint))
+            cells_hist = (1 + 2 * ntr) * sweep_cells
+            hist = {"value": weak_scaling_value(cells_hist, world, hms) / 1e9, "unit": UNIT,
                     "h_applies_per_s": weak_scaling_value(wl.trials.shape[0], world, hms),
                     "ms_per_h": hms, "steps": nh,
                     "history_bytes": int(wl.ns * (wl.nt - 1) * wl.cells_padded() * 4),
@@ -441,7 +458,7 @@ def main():
         torch.cuda.synchronize(dev)
         per_shot_ms = ep0.elapsed_time(ep1) / nsub
         plain_ms = per_shot_ms * wl.ns
-        plain = {"value": cells_per_h / (plain_ms * 1e-3) / 1e9, "unit": UNIT,
+        plain = {"value": cells_plain / (plain_ms * 1e-3) / 1e9, "unit": UNIT,
                  "h_applies_per_s": wl.trials.shape[0] / (plain_ms * 1e-3),
                  "ms_per_h": plain_ms,
                  "how": f"one shot resident at a time, timed on {nsub} shots and scaled to {wl.ns}"}
@@ -485,7 +502,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
         "plain": plain,
-        "batched_over_plain": (value / plain["value"]) if plain else None,
+        "batched_over_plain": (h_per_s / plain["h_applies_per_s"]) if plain else None,  # in H-applies/s
         "dtt_history": hist,
         "stated_error": {"fp32_dot_test": dot_err,
                          "hv_vs_oracle": "see tests/test_gpu_parity.py (1e-4 FP32, 2e-3 16-bit)"},

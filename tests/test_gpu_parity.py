@@ -266,6 +266,12 @@ def test_config2_full_size_dot_and_hessian_consistency(cuda_device, cfg2):
     rhs = float(torch.sum(dm.double() * img.double()))
     assert abs(lhs - rhs) / lhs < 1e-5
     assert rel(hd.cpu().numpy(), img.cpu().numpy()) < 1e-5
+    # the bench's batched path (FP16 checkpoints, autotuned, graphs) at full size: within the
+    # 16-bit bound of the FP32-checkpoint H, itself within 1e-4 of the oracle (sampled test above)
+    p16 = make_probe(wl, snapshot_dtype="fp16")
+    p16.set_option("use_graph", 1)
+    h16 = p16.apply_H(dm)
+    assert rel(h16.cpu().numpy(), hd.cpu().numpy()) < 2e-3
 
 
 def test_bounded_wait_reports_timeout_and_context_survives(cuda_device):
