@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--pipeline", type=int, default=-1,
                     help="with --profile: 0 one tile per CTA, 2 or 3 pipelined kernels (-1: autotuned)")
     ap.add_argument("--pipe-rows", type=int, default=0, help="with --pipeline 2/3: rows per thread (1 or 2)")
+    ap.add_argument("--mini", default="",
+                    help="with --profile: reduced grid of the same recipe, 'NZxNX[xNY]:NT' (interior "
+                         "shape and time steps), e.g. 128x128x128:40 for a few-GB 3D capture")
     ap.add_argument("--fixed", default="",
                     help="pf,pa,R,G: fixed forward / adjoint kernel variants, rows per thread and shots "
                          "per adjoint CTA instead of the autotuner (for runs under a profiler)")
@@ -77,7 +80,8 @@ def profile_run(a, wl):
     dev = torch.device("cuda", 0)
     p = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet, snapshot_dtype=a.snapshot)
     p.set_option("check_finite", 0)
-    p.set_option("tile_z", 16)
+    if len(wl.shape) == 2:
+        p.set_option("tile_z", 16)
     if a.pipeline >= 0:               # fixed kernel variant (no timing under the profiler)
         p.set_option("pipeline", a.pipeline)
         if a.pipe_rows:
@@ -254,8 +258,13 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
-    from workloads import CONFIG_NAMES, make_config
-    wl = make_config(a.config)
+    from workloads import CONFIG_NAMES, make_config, mini_config
+    if a.mini and a.profile:
+        shape_s, nt_s = a.mini.split(":")
+        wl = mini_config(a.config, shape=tuple(int(v) for v in shape_s.split("x")), nt=int(nt_s),
+                         ns=a.shots or None)
+    else:
+        wl = make_config(a.config)
     if a.shots:
         wl.src = wl.src[:a.shots]
     if a.profile:

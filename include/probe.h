@@ -124,8 +124,10 @@ typedef enum {
                                     (forward and adjoint kernel, pipeline depth, rows per thread, shot group)
                                     and keep the fastest; setting PROBE_OPT_PIPELINE, PROBE_OPT_PIPE_ROWS or
                                     PROBE_OPT_SHOT_GROUP turns it off */
-    PROBE_OPT_PIPE_ROWS = 10,    /* 2D pipelined kernels: rows per thread R, tile 64 x 16R (1 or 2) */
-    PROBE_OPT_PIPELINE_ADJ = 11  /* 2D adjoint kernel only (0, 2 or 3; PROBE_OPT_PIPELINE sets both) */
+    PROBE_OPT_PIPE_ROWS = 10,    /* 2D pipelined kernels: rows per thread R, tile 64 x 16R (1 or 2),
+                                    forward and adjoint */
+    PROBE_OPT_PIPELINE_ADJ = 11, /* 2D adjoint kernel only (0, 2 or 3; PROBE_OPT_PIPELINE sets both) */
+    PROBE_OPT_PIPE_ROWS_ADJ = 12 /* 2D pipelined adjoint only: rows per thread (1 or 2) */
 } probe_option;
 
 /* Counters and timings of the last apply call (probe_get_stats). */
@@ -151,7 +153,8 @@ typedef struct {
     int pipeline_forward;        /* 2D forward kernel: 0 one tile per CTA, 2..4 pipeline stages */
     int pipeline_adjoint;        /* 2D adjoint kernel: same encoding */
     int dtt_history;             /* 1 when Dtt u^n of every step was kept instead of recomputed */
-    int pipeline_rows;           /* rows per thread of the pipelined kernels (0: not pipelined) */
+    int pipeline_rows;           /* rows per thread of the pipelined forward kernels (0: not pipelined) */
+    int pipeline_rows_adjoint;   /* rows per thread of the pipelined adjoint kernel */
 } probe_stats;
 
 /* Create a handle for one background model and acquisition geometry.

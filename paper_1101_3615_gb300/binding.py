@@ -21,7 +21,7 @@ STATUS = {0: "PROBE_OK", -1: "PROBE_ERR_ARG", -2: "PROBE_ERR_CUDA", -3: "PROBE_E
           -4: "PROBE_ERR_TIMEOUT", -5: "PROBE_ERR_NONFINITE", -6: "PROBE_ERR_STATE"}
 SNAP = {"fp32": 0, "bf16": 1, "fp16": 2}
 OPT = {"check_finite": 1, "shot_wave": 2, "shot_group": 3, "use_graph": 4, "timing": 5, "tile_z": 6,
-       "pipeline": 7, "dtt_history": 8, "autotune": 9, "pipe_rows": 10, "pipeline_adj": 11}
+       "pipeline": 7, "dtt_history": 8, "autotune": 9, "pipe_rows": 10, "pipeline_adj": 11, "pipe_rows_adj": 12}
 
 
 class probe_grid(C.Structure):
@@ -45,7 +45,8 @@ class probe_stats(C.Structure):
                 ("bytes_recompute", C.c_double), ("bytes_adjoint", C.c_double),
                 ("shot_wave", C.c_int), ("shot_group", C.c_int), ("tile_z", C.c_int),
                 ("ckpt_stride", C.c_int), ("pipeline_forward", C.c_int),
-                ("pipeline_adjoint", C.c_int), ("dtt_history", C.c_int), ("pipeline_rows", C.c_int)]
+                ("pipeline_adjoint", C.c_int), ("dtt_history", C.c_int), ("pipeline_rows", C.c_int),
+                ("pipeline_rows_adjoint", C.c_int)]
 
 
 class ProbeError(RuntimeError):

@@ -12,6 +12,12 @@
 
 namespace probe {
 
+struct WsMaps {
+    CUtensorMap wu, wf;                      // halo boxes (64 + 8) x (16 rows + 8): incident, Born/adjoint
+    CUtensorMap up, fp, dmp, dtp, img, cmp;  // plain 64 x 16 rows boxes
+    int rows = 0;                            // R (0: not encoded)
+};
+
 struct Workspace {
     // sizing key
     int W = 0, nb = 0, with_ckpt = 0, with_data = 0, groups = 0;
@@ -31,10 +37,9 @@ struct Workspace {
     float* s_tmp = nullptr;   // [F]
     int* src_wave = nullptr;  // [W][2] padded sources of the wave
     CUtensorMap tm_u, tm_f;
-    // pipelined kernels: halo and plain boxes for tiles of 64 x 16 map_rows
-    CUtensorMap tm_wu, tm_wf;
-    CUtensorMap tm_up, tm_fp, tm_dmp, tm_dtp;
-    int map_rows = 0;
+    // pipelined kernels: halo and plain boxes for tiles of 64 x 16 rows, one set for the
+    // forward kernels and one for the adjoint (their row counts are chosen separately)
+    WsMaps mf, ma;
     int tm_tile_z = 0;
     long long generation = 0;
 };
@@ -42,7 +47,7 @@ struct Workspace {
 // A captured sweep (forward + adjoint of one wave) and the key it was captured for.
 struct TunedEntry {
     std::vector<long long> key;  // kind, adjoint, then shots and trials of each model (and handles for groups)
-    int pipe_fwd = 2, pipe_adj = 2, group = 4, rows = 2;
+    int pipe_fwd = 2, pipe_adj = 2, group = 4, rows = 2, rows_adj = 1;
 };
 
 struct GraphEntry {
@@ -85,7 +90,8 @@ struct probe_s {
     // receivers by pipelined-kernel tile (64 x 16R), R = 1, 2
     int* d_wrec_ptr[3] = {nullptr, nullptr, nullptr};
     int* d_wrec_idx[3] = {nullptr, nullptr, nullptr};
-    int ws_rows = 2;             // rows per thread R of the pipelined kernels
+    int ws_rows = 2;             // rows per thread R of the pipelined forward kernels
+    int ws_rows_adj = 1;         // and of the pipelined adjoint kernels
     int* d_err = nullptr;
     probe::Workspace ws;
     probe::DevBuf stage_in, stage_out;

@@ -37,6 +37,8 @@ struct alignas(128) ModelStep2D {
     CUtensorMap tm_sp;   // s, one plane, plain box
     CUtensorMap tm_dmp;  // dm, nb planes, plain box
     CUtensorMap tm_dtp;  // Dtt segment buffer, W * dtt_slots planes, plain box
+    CUtensorMap tm_img;  // images [groups][nb] planes, plain box (pipelined adjoint)
+    CUtensorMap tm_cmp;  // their Kahan compensation
     int Nz, Nx, P, pad, nz, nx;
     int tiles_x, tiles_z, ntiles;
     int ws_rows;                 // pipelined kernels: rows per thread R (tile height 16R)
@@ -105,6 +107,7 @@ struct alignas(128) ModelStep3D {
     int nr;
     float cz, cy, cx;
     float lz[4], ly[4], lx[4];
+    float cxm[4];        // x taps in first-difference form, sum_{k>m} w_k / hx^2
     float inv_dt2, vol_inv;
     long long F;         // floats per volume (Nz * Ny * P)
     float* state;

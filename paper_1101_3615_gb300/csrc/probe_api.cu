@@ -184,17 +184,21 @@ int pick_group(probe_t h, int W) {
 }
 
 // Tensor maps of the pipelined kernels for tiles of 64 x 16R (host-side encoding only).
-probe_status encode_ws_maps(probe_t h, int R) {
+probe_status encode_ws_maps(probe_t h, WsMaps& m, int R) {
     Workspace& w = h->ws;
     const int rows = 16 * R;
     const int nb = std::max(w.nb, 1);
-    TRY(encode_planes(h, &w.tm_wu, w.u, w.W * 2, rows));
-    TRY(encode_planes(h, &w.tm_wf, w.f, w.W * nb * 2, rows));
-    TRY(encode_plain(h, &w.tm_up, w.u, w.W * 2, rows));
-    TRY(encode_plain(h, &w.tm_fp, w.f, w.W * nb * 2, rows));
-    TRY(encode_plain(h, &w.tm_dmp, w.dm, nb, rows));
-    if (w.dtt) TRY(encode_plain(h, &w.tm_dtp, w.dtt, w.W * w.dtt_slots, rows));
-    w.map_rows = R;
+    TRY(encode_planes(h, &m.wu, w.u, w.W * 2, rows));
+    TRY(encode_planes(h, &m.wf, w.f, w.W * nb * 2, rows));
+    TRY(encode_plain(h, &m.up, w.u, w.W * 2, rows));
+    TRY(encode_plain(h, &m.fp, w.f, w.W * nb * 2, rows));
+    TRY(encode_plain(h, &m.dmp, w.dm, nb, rows));
+    if (w.dtt) TRY(encode_plain(h, &m.dtp, w.dtt, w.W * w.dtt_slots, rows));
+    if (w.img) {
+        TRY(encode_plain(h, &m.img, w.img, w.groups * nb, rows));
+        TRY(encode_plain(h, &m.cmp, w.comp, w.groups * nb, rows));
+    }
+    m.rows = R;
     return PROBE_OK;
 }
 
@@ -248,7 +252,10 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     w.groups = G;
     TRY(encode_planes(h, &w.tm_u, w.u, W * 2, h->tile_z));
     TRY(encode_planes(h, &w.tm_f, w.f, W * std::max(nb, 1) * 2, h->tile_z));
-    if (h->ndim == 2) TRY(encode_ws_maps(h, h->ws_rows));
+    if (h->ndim == 2) {
+        TRY(encode_ws_maps(h, w.mf, h->ws_rows));
+        TRY(encode_ws_maps(h, w.ma, h->ws_rows_adj));
+    }
     w.tm_tile_z = h->tile_z;
     return PROBE_OK;
 }
@@ -327,20 +334,23 @@ struct Job {
     int groups = 1, shot_group = 1;
 };
 
-void fill_model(const Job& jb, ModelStep2D& m, int* blocks_fwd, int* blocks_adj) {
+// One model's parameter block; maps: the pipelined-kernel tensor maps (forward or adjoint set).
+void fill_model(const Job& jb, ModelStep2D& m, const WsMaps& maps, int* blocks_fwd, int* blocks_adj) {
     probe_t h = jb.h;
     Workspace& w = h->ws;
     m.tm_u = w.tm_u;
     m.tm_f = w.tm_f;
-    m.tm_wu = w.tm_wu;
-    m.tm_wf = w.tm_wf;
-    m.tm_up = w.tm_up;
-    m.tm_fp = w.tm_fp;
-    m.tm_dmp = w.tm_dmp;
-    m.tm_dtp = w.tm_dtp;
+    m.tm_wu = maps.wu;
+    m.tm_wf = maps.wf;
+    m.tm_up = maps.up;
+    m.tm_fp = maps.fp;
+    m.tm_dmp = maps.dmp;
+    m.tm_dtp = maps.dtp;
+    m.tm_img = maps.img;
+    m.tm_cmp = maps.cmp;
     m.dtt_slots = w.dtt_slots;
     m.dtt_store = w.history;
-    const int R = w.map_rows > 0 ? w.map_rows : 1;
+    const int R = maps.rows > 0 ? maps.rows : 1;
     m.ws_rows = R;
     m.ws_tiles_z = (h->Nz + 16 * R - 1) / (16 * R);
     m.ws_ntiles = m.ws_tiles_z * h->tiles_x;
@@ -404,7 +414,8 @@ void fill_model(const Job& jb, ModelStep2D& m, int* blocks_fwd, int* blocks_adj)
 
 struct Sweep {
     std::vector<Job> jobs;
-    StepParams2D p;
+    StepParams2D p;   // forward launches
+    StepParams2D pa;  // adjoint launches (the pipelined adjoint may use another tile height)
     int blocks_fwd = 0, blocks_adj = 0;
     int nbc = 1, chunks = 1;
     int tile_z = 16;
@@ -421,6 +432,10 @@ probe_status prepare_sweep(Sweep& sw, probe_t h0, cudaStream_t st) {
     sw.p.nmodels = (int)sw.jobs.size();
     sw.p.nt = h0->nt;
     sw.p.err = h0->d_err;
+    memset(&sw.pa, 0, sizeof(sw.pa));
+    sw.pa.nmodels = sw.p.nmodels;
+    sw.pa.nt = sw.p.nt;
+    sw.pa.err = sw.p.err;
     sw.st = st;
     sw.nt = h0->nt;
     sw.K = h0->K;
@@ -431,17 +446,22 @@ probe_status prepare_sweep(Sweep& sw, probe_t h0, cudaStream_t st) {
     sw.kahan = h0->kahan != 0;
     int maxnb = 1;
     std::vector<int> bf(sw.jobs.size()), ba(sw.jobs.size());
-    for (Job& jb : sw.jobs)  // every model of a launch uses the first one's pipelined tile height
-        if (jb.h->ndim == 2 && jb.h->ws.u && jb.h->ws.map_rows != h0->ws_rows) TRY(encode_ws_maps(jb.h, h0->ws_rows));
+    for (Job& jb : sw.jobs) {  // every model of a launch uses the first one's pipelined tile heights
+        Workspace& w = jb.h->ws;
+        if (jb.h->ndim != 2 || !w.u) continue;
+        if (w.mf.rows != h0->ws_rows) TRY(encode_ws_maps(jb.h, w.mf, h0->ws_rows));
+        if (w.ma.rows != h0->ws_rows_adj) TRY(encode_ws_maps(jb.h, w.ma, h0->ws_rows_adj));
+    }
     for (size_t k = 0; k < sw.jobs.size(); ++k) {
         int f, a;
-        fill_model(sw.jobs[k], sw.p.m[k], &f, &a);
+        fill_model(sw.jobs[k], sw.pa.m[k], sw.jobs[k].h->ws.ma, &f, &a);
+        fill_model(sw.jobs[k], sw.p.m[k], sw.jobs[k].h->ws.mf, &f, &a);
         bf[k] = f;
         ba[k] = a;
         maxnb = std::max(maxnb, sw.jobs[k].nb);
     }
     sw.nbc = maxnb <= 1 ? 1 : (maxnb <= 2 ? 2 : (maxnb <= 4 ? 4 : 8));
-    if (sw.pipeline_adj && sw.tile_z == kPipeTZ && h0->ws_rows == 2) sw.nbc = std::min(sw.nbc, 4);
+    if (sw.pipeline_adj && sw.tile_z == kPipeTZ && h0->ws_rows_adj == 2) sw.nbc = std::min(sw.nbc, 4);
     sw.chunks = (maxnb + sw.nbc - 1) / sw.nbc;
     // block_begin differs between the forward and the adjoint grids; kept for
     // the forward here and rewritten by set_grid().
@@ -456,16 +476,17 @@ probe_status prepare_sweep(Sweep& sw, probe_t h0, cudaStream_t st) {
 
 void set_grid(Sweep& sw, bool adjoint) {
     const bool ws = (adjoint ? sw.pipeline_adj : sw.pipeline) && sw.tile_z == kPipeTZ;
+    StepParams2D& p = adjoint ? sw.pa : sw.p;
     int b = 0, items = 0;
     for (size_t k = 0; k < sw.jobs.size(); ++k) {
         const Job& jb = sw.jobs[k];
         const int units = adjoint ? jb.groups : jb.W;
-        sw.p.m[k].block_begin = b;
-        sw.p.m[k].item_begin = items;
+        p.m[k].block_begin = b;
+        p.m[k].item_begin = items;
         b += units;
-        items += units * (ws ? sw.p.m[k].ws_ntiles : jb.h->ntiles);
+        items += units * (ws ? p.m[k].ws_ntiles : jb.h->ntiles);
     }
-    sw.p.total_items = items;
+    p.total_items = items;
 }
 
 probe_status launch_fwd_step(Sweep& sw, FwdKind kind, int n, int slot) {
@@ -480,11 +501,11 @@ probe_status launch_fwd_step(Sweep& sw, FwdKind kind, int n, int slot) {
 
 probe_status launch_adj_step(Sweep& sw, int n, int slot) {
     set_grid(sw, true);
-    sw.p.n = n;
-    for (int k = 0; k < sw.p.nmodels; ++k) sw.p.m[k].dtt_slot = slot;
+    sw.pa.n = n;
+    for (int k = 0; k < sw.pa.nmodels; ++k) sw.pa.m[k].dtt_slot = slot;
     cudaError_t e = (sw.pipeline_adj && sw.tile_z == kPipeTZ)
-                        ? launch_adj2d_pipe(sw.nbc, sw.kahan, sw.pipeline_adj, sw.p, sw.chunks, sw.st)
-                        : launch_adj2d(sw.tile_z, sw.nbc, sw.kahan, sw.p, sw.blocks_adj, sw.chunks, sw.st);
+                        ? launch_adj2d_pipe(sw.nbc, sw.kahan, sw.pipeline_adj, sw.pa, sw.chunks, sw.st)
+                        : launch_adj2d(sw.tile_z, sw.nbc, sw.kahan, sw.pa, sw.blocks_adj, sw.chunks, sw.st);
     if (e != cudaSuccess) return cuda_fail(sw.jobs[0].h, e, "adjoint step launch");
     return PROBE_OK;
 }
@@ -622,6 +643,11 @@ void fill3d(const Job& jb, ModelStep3D& m) {
         m.lz[k] = (float)(wk[k] / (h->hz * h->hz));
         m.ly[k] = (float)(wk[k] / (h->hy * h->hy));
         m.lx[k] = (float)(wk[k] / (h->hx * h->hx));
+    }
+    for (int mm = 0; mm < 4; ++mm) {  // first-difference x taps: sum_{k>m} w_k / hx^2
+        double cm = 0.0;
+        for (int k = mm; k < 4; ++k) cm += wk[k];
+        m.cxm[mm] = (float)(cm / (h->hx * h->hx));
     }
     m.inv_dt2 = (float)(1.0 / (h->dt * h->dt));
     m.vol_inv = (float)(1.0 / (h->hz * h->hy * h->hx));
@@ -1080,8 +1106,10 @@ extern "C" probe_status probe_set_option(probe_t h, int key, long long v) {
             h->user_fixed = 1;
             return PROBE_OK;
         case PROBE_OPT_PIPE_ROWS:
+        case PROBE_OPT_PIPE_ROWS_ADJ:
             if (v != 1 && v != 2) return fail(h, PROBE_ERR_ARG, "pipelined rows per thread must be 1 or 2");
-            h->ws_rows = (int)v;
+            if (key == PROBE_OPT_PIPE_ROWS) h->ws_rows = (int)v;
+            h->ws_rows_adj = (int)v;
             h->user_fixed = 1;
             return PROBE_OK;
         case PROBE_OPT_USE_GRAPH: h->opt_use_graph = v ? 1 : 0; return PROBE_OK;
@@ -1214,6 +1242,7 @@ probe_status autotune_2d(probe_t h, const std::vector<long long>& key, std::vect
             h->opt_pipeline = t.pipe_fwd;
             h->pipe_adj = t.pipe_adj;
             h->ws_rows = t.rows;
+            h->ws_rows_adj = t.rows_adj;
             *group = t.group;
             return PROBE_OK;
         }
@@ -1232,6 +1261,7 @@ probe_status autotune_2d(probe_t h, const std::vector<long long>& key, std::vect
     };
     probe_status rc = PROBE_OK;
     int best_fwd = h->opt_pipeline, best_adj = h->pipe_adj, best_grp = std::min(4, maxW), best_rows = h->ws_rows;
+    int best_rows_adj = h->ws_rows_adj;
     // candidates are timed round-robin, three rounds, keeping each one's fastest round
     constexpr int kRounds = 3, kReps = 24;
     {
@@ -1264,15 +1294,14 @@ probe_status autotune_2d(probe_t h, const std::vector<long long>& key, std::vect
         std::vector<Cand> cand;
         for (int grp : {1, 2, 4, 8}) {
             if (grp > 1 && grp >= 2 * maxW) continue;
-            cand.push_back({0, best_rows, grp});
-            for (int R : {1, 2})
-                if (best_fwd == 0 || R == best_rows) cand.push_back({2, R, grp});
+            cand.push_back({0, 1, grp});
+            for (int R : {1, 2}) cand.push_back({2, R, grp});
         }
         std::vector<float> t(cand.size(), 1e30f);
         for (int r = 0; r < kRounds && rc == PROBE_OK; ++r)
             for (size_t c = 0; c < cand.size() && rc == PROBE_OK; ++c) {
                 h->pipe_adj = cand[c].pipe;
-                h->ws_rows = cand[c].rows;
+                h->ws_rows_adj = cand[c].rows;
                 Sweep sw;
                 float ms = 0.f;
                 if ((rc = sweep_for(cand[c].grp, &sw)) != PROBE_OK) break;
@@ -1287,10 +1316,11 @@ probe_status autotune_2d(probe_t h, const std::vector<long long>& key, std::vect
             const Cand& bc = cand[(size_t)(std::min_element(t.begin(), t.end()) - t.begin())];
             best_adj = bc.pipe;
             best_grp = bc.grp;
-            if (bc.pipe) best_rows = bc.rows;
+            if (bc.pipe) best_rows_adj = bc.rows;
         }
     }
     h->ws_rows = best_rows;
+    h->ws_rows_adj = best_rows_adj;
     h->opt_timing = saved_timing;
     h->opt_pipeline = best_fwd;
     h->pipe_adj = best_adj;
@@ -1302,6 +1332,7 @@ probe_status autotune_2d(probe_t h, const std::vector<long long>& key, std::vect
     t.pipe_adj = best_adj;
     t.group = best_grp;
     t.rows = best_rows;
+    t.rows_adj = best_rows_adj;
     h->tuned.push_back(t);
     return PROBE_OK;
 }
@@ -1392,6 +1423,7 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
             h->stats.pipeline_forward = piped ? h->opt_pipeline : 0;
             h->stats.pipeline_adjoint = piped ? h->pipe_adj : 0;
             h->stats.pipeline_rows = piped ? h->ws_rows : 0;
+            h->stats.pipeline_rows_adjoint = piped ? h->ws_rows_adj : 0;
             if (need_ckpt) {
                 CK(h, cudaMemsetAsync(w.img, 0, (size_t)G * nbw * h->F * 4, st));
                 CK(h, cudaMemsetAsync(w.comp, 0, (size_t)G * nbw * h->F * 4, st));
@@ -1413,7 +1445,7 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
             sw.jobs.push_back(jb);
             const std::vector<long long> key = {(long long)op, (long long)kind, (long long)need_ckpt, Wv, nbw, j0,
                                                 (long long)(size_t)jb.data, (long long)(size_t)jb.rdata,
-                                                (long long)(size_t)jb.s, h->ws.generation, h->opt_pipeline, h->pipe_adj, h->ws_rows, h->opt_timing,
+                                                (long long)(size_t)jb.s, h->ws.generation, h->opt_pipeline, h->pipe_adj, h->ws_rows, h->ws_rows_adj, h->opt_timing,
                                                 jb.shot_group, h->tile_z, h->nt};
             long long cnt[4] = {0, 0, 0, 0};
             TRY(run_maybe_graph(h, key, st, cnt, [&](cudaStream_t ss) -> probe_status {
@@ -1722,6 +1754,7 @@ extern "C" probe_status probe_apply_H_group(const probe_t* models, int nmodels, 
     h0->stats.pipeline_forward = h0->tile_z == kPipeTZ ? h0->opt_pipeline : 0;
     h0->stats.pipeline_adjoint = h0->tile_z == kPipeTZ ? h0->pipe_adj : 0;
     h0->stats.pipeline_rows = h0->tile_z == kPipeTZ ? h0->ws_rows : 0;
+    h0->stats.pipeline_rows_adjoint = h0->tile_z == kPipeTZ ? h0->ws_rows_adj : 0;
     if (h0->opt_timing) TRY(ensure_events(h0, 3 + 2 * h0->nck + 2));
     // the whole group's sweeps as one graph (cached on h0 by handles, workspaces and variants)
     std::vector<long long> gkey = key;
@@ -1732,6 +1765,7 @@ extern "C" probe_status probe_apply_H_group(const probe_t* models, int nmodels, 
     gkey.push_back(h0->opt_pipeline);
     gkey.push_back(h0->pipe_adj);
     gkey.push_back(h0->ws_rows);
+    gkey.push_back(h0->ws_rows_adj);
     gkey.push_back(h0->opt_timing);
     gkey.push_back(h0->tile_z);
     long long cnt[4] = {0, 0, 0, 0};

@@ -42,7 +42,9 @@ struct Ws {
     static constexpr int HALO = HX * HZ;    // floats
     static constexpr int PLAIN = kTX * TZ;  // floats
     static constexpr int FWD_STAGE = HALO + 2 * PLAIN;
-    static constexpr int ADJ_STAGE = HALO + 4 * PLAIN;  // mu^{n+2}, Dtt, s, injection tile
+    // adjoint stage: halo of mu^{n+1}, mu^{n+2}, Dtt, s, then either the injection tile or the
+    // image and compensation tiles of a trial's last group (a receiver tile reads its image from HBM)
+    static constexpr int ADJ_STAGE = HALO + 5 * PLAIN;
     static constexpr unsigned HALO_B = HALO * 4u, PLAIN_B = PLAIN * 4u;
 };
 
@@ -406,15 +408,21 @@ __global__ void __launch_bounds__(kWsThreads, (NBC * R >= 8) ? 1 : 2) k_adj2d_ws
                         gi.inj = inj;
                         info[s] = gi;
                         const int pl = (shot * M.nb + b) * 2;
-                        const bool with_d = bi == 0, with_s = (jj == 0) && (bi == 0);
+                        const bool with_d = bi == 0, with_s = (jj == 0) && (bi == 0), with_i = gi.last && !inj;
                         mbar_expect_tx(&full[s], T::HALO_B + T::PLAIN_B + (with_d ? T::PLAIN_B : 0u) +
-                                                     (with_s ? T::PLAIN_B : 0u));
+                                                     (with_s ? T::PLAIN_B : 0u) +
+                                                     (with_i ? (KAHAN ? 2u : 1u) * T::PLAIN_B : 0u));
                         tma_load_3d(st, &M.tm_wf, q.x0 - 4, q.z0 - 4, pl + pc, &full[s]);
                         tma_load_3d(st + T::HALO, &M.tm_fp, q.x0, q.z0, pl + po, &full[s]);
                         if (with_d)
                             tma_load_3d(st + T::HALO + T::PLAIN, &M.tm_dtp, q.x0, q.z0,
                                         shot * M.dtt_slots + M.dtt_slot, &full[s]);
                         if (with_s) tma_load_3d(st + T::HALO + 2 * T::PLAIN, &M.tm_sp, q.x0, q.z0, 0, &full[s]);
+                        if (with_i) {  // trial b's image tile (and compensation), added to at this group
+                            const int ip = q.unit * M.nb + b;
+                            tma_load_3d(st + T::HALO + 3 * T::PLAIN, &M.tm_img, q.x0, q.z0, ip, &full[s]);
+                            if (KAHAN) tma_load_3d(st + T::HALO + 4 * T::PLAIN, &M.tm_cmp, q.x0, q.z0, ip, &full[s]);
+                        }
                     }
                     __syncwarp();
                     if (++s == S) {
@@ -490,13 +498,7 @@ __global__ void __launch_bounds__(kWsThreads, (NBC * R >= 8) ? 1 : 2) k_adj2d_ws
                 st4(M.f + (long long)((shot * M.nb + b) * 2 + po) * M.F + (long long)z * M.P + x,
                     make_float4(o[0], o[1], o[2], o[3]));
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-        if (++s == S) {
-            s = 0;
-            ph ^= 1u;
-        }
-        if (q.last) {  // trial b's sum over the shot group is complete: add it to its image
+        if (q.last) {  // trial b's sum over the shot group is complete: add it to its image tile
             float* img = M.img + (long long)q.unit * M.img_group_stride + (long long)b * M.F;
             float* cmp = M.comp + (long long)q.unit * M.img_group_stride + (long long)b * M.F;
 #pragma unroll
@@ -507,9 +509,10 @@ __global__ void __launch_bounds__(kWsThreads, (NBC * R >= 8) ? 1 : 2) k_adj2d_ws
                         const int z = q.z0 + lz + r;
                         if (fast || (z < M.Nz && x < M.Nx)) {
                             const long long off = (long long)z * M.P + x;
-                            float4 iv = ld4(img + off);
+                            const float* ist = st + T::HALO + 3 * T::PLAIN + (lz + r) * kTX + lx;
+                            float4 iv = q.inj ? ld4(img + off) : ld4(ist);
                             if (KAHAN) {
-                                float4 cv = ld4(cmp + off);
+                                float4 cv = q.inj ? ld4(cmp + off) : ld4(ist + T::PLAIN);
                                 kahan4(iv, cv, acc[k][r][0], acc[k][r][1], acc[k][r][2], acc[k][r][3]);
                                 st4(cmp + off, cv);
                             } else {
@@ -524,6 +527,12 @@ __global__ void __launch_bounds__(kWsThreads, (NBC * R >= 8) ? 1 : 2) k_adj2d_ws
                         for (int j = 0; j < 4; ++j) acc[k][r][j] = 0.f;
                     }
                 }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == S) {
+            s = 0;
+            ph ^= 1u;
         }
     }
 }

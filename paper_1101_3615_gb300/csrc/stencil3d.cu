@@ -21,6 +21,7 @@ namespace probe {
 
 constexpr int kTY3 = kTY3D;
 constexpr int kRing = 10;
+constexpr int kPrefetch3 = 2;   // planes ahead whose pointwise operands are prefetched into L2
 constexpr int kHX3 = kTX + 8;   // 72
 constexpr int kHY3 = kTY3 + 8;  // 24
 constexpr int kPlane3 = kHX3 * kHY3;
@@ -35,10 +36,46 @@ __device__ __forceinline__ float sponge_e3(const ModelStep3D& M, int z, int y, i
     return __fmaf_rn(M.cz, (float)(rz * rz), __fmaf_rn(M.cy, (float)(ry * ry), __fmul_rn(M.cx, (float)(rx * rx))));
 }
 
+// Pointwise operands of one plane of a thread's 4 cells, loaded one plane ahead of their use
+// so that their HBM latency overlaps the previous plane's work.
+struct Pw3 {
+    float4 s, prev, d, dm, img, cmp;
+};
+
 template <int MODE, bool KAHAN>
-__global__ void __launch_bounds__(kThreads) k_step3d(const __grid_constant__ StepParams3D p) {
+__device__ __forceinline__ void load_pw3(const ModelStep3D& M, const float* outv, long long off, int shot, int b,
+                                         long long F, Pw3& w) {
+    w.s = ld4(M.s + off);
+    w.prev = ld4(outv + off);
+    if (MODE == STEP3_BORN || MODE == STEP3_ADJ) w.d = ld4(M.Din + (long long)shot * M.Din_shot_stride + off);
+    if (MODE == STEP3_BORN) w.dm = ld4(M.dm + (long long)b * F + off);
+    if (MODE == STEP3_ADJ) {
+        w.img = ld4(M.img + (long long)(shot * M.nfield + b) * F + off);
+        if (KAHAN) w.cmp = ld4(M.comp + (long long)(shot * M.nfield + b) * F + off);
+    }
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// The same operands two planes ahead, brought into L2 only (no registers held).
+template <int MODE, bool KAHAN>
+__device__ __forceinline__ void prefetch_pw3(const ModelStep3D& M, const float* outv, long long off, int shot, int b,
+                                             long long F) {
+    prefetch_l2(M.s + off);
+    prefetch_l2(outv + off);
+    if (MODE == STEP3_BORN || MODE == STEP3_ADJ) prefetch_l2(M.Din + (long long)shot * M.Din_shot_stride + off);
+    if (MODE == STEP3_BORN) prefetch_l2(M.dm + (long long)b * F + off);
+    if (MODE == STEP3_ADJ) {
+        prefetch_l2(M.img + (long long)(shot * M.nfield + b) * F + off);
+        if (KAHAN) prefetch_l2(M.comp + (long long)(shot * M.nfield + b) * F + off);
+    }
+}
+
+template <int MODE, bool KAHAN>
+__global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ StepParams3D p) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bars[kRing];
+    constexpr bool RECV = (MODE != STEP3_INC);  // receivers: sampling (Born, nonlinear) or injection (adjoint)
     const ModelStep3D& M = p.m;
     const int tid = threadIdx.x;
     const int lx = (tid & 15) << 2, ly = tid >> 4;
@@ -59,7 +96,8 @@ __global__ void __launch_bounds__(kThreads) k_step3d(const __grid_constant__ Ste
     const int vol_cur = shot * M.nvol_shot + 2 * b + pc;
     float* outv = M.state + (long long)(shot * M.nvol_shot + 2 * b + po) * F;
     float* sinj = smem + kRing * kPlane3;
-    const int nplanes = (zend - z0) + 8;
+    const int nloc = zend - z0;
+    const int nplanes = nloc + 8;
 
     if (tid == 0) {
         for (int i = 0; i < kRing; ++i) mbar_init(&bars[i], 1);
@@ -81,28 +119,43 @@ __global__ void __launch_bounds__(kThreads) k_step3d(const __grid_constant__ Ste
     const int sx = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.src[3 * shot + 2] : -1;
     const float fsrc = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.wavelet[n] * M.vol_inv : 0.f;
     const int tile_xy = tyi * M.tiles_x + txi;
+    const long long plane_stride = (long long)M.Ny * M.P;
+    const long long off0 = ((long long)z0 * M.Ny + y) * M.P + x;
 
-    for (int iz = 0; iz < zend - z0; ++iz) {
+    // ring bookkeeping without divisions: slot of the current plane (k = iz + 4) and of the
+    // farthest plane the taps need (k = iz + 8), with that slot's mbarrier phase
+    int slot_c = 4, slot_w = 8;
+    uint32_t ph_w = 0;
+
+    // one z plane; the operands of this plane arrived in cur_pw, the next plane's go to nxt_pw
+    auto plane = [&](int iz, const Pw3& cur_pw, Pw3& nxt_pw) -> bool {
         const int z = z0 + iz;
-        // all planes up to k = iz + 8 must have landed
+        if (col_ok && iz + 1 < nloc)  // next plane's operands, in flight during this plane
+            load_pw3<MODE, KAHAN>(M, outv, off0 + (long long)(iz + 1) * plane_stride, shot, b, F, nxt_pw);
+        if (col_ok && iz + kPrefetch3 < nloc)
+            prefetch_pw3<MODE, KAHAN>(M, outv, off0 + (long long)(iz + kPrefetch3) * plane_stride, shot, b, F);
+        // every plane up to k = iz + 8 must have landed
         const int kfirst = (iz == 0) ? 0 : iz + 8;
         for (int k = kfirst; k <= iz + 8; ++k) {
-            const bool ok = mbar_wait_bounded(&bars[k % kRing], (uint32_t)((k / kRing) & 1));
+            const bool ok = (iz == 0) ? mbar_wait_bounded(&bars[k], 0u) : mbar_wait_bounded(&bars[slot_w], ph_w);
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) {
                     // flag the error, then give the copies still in flight one more bounded wait
                     set_dev_error(p.err, DEVERR_TIMEOUT);
-                    const int issued = min(nplanes, iz - 1 + kRing + 1);
+                    const int issued = min(nplanes, iz + kRing);
                     for (int q = k; q < issued; ++q)
                         (void)mbar_wait_bounded(&bars[q % kRing], (uint32_t)((q / kRing) & 1));
                 }
-                return;
+                return false;
             }
         }
-        // receivers of this plane (Born sampling / adjoint injection)
-        const int rk = tile_xy * M.Nz + z;
-        const int rbeg = M.rec_ptr[rk], rend = M.rec_ptr[rk + 1];
-        const float* cur = smem + ((iz + 4) % kRing) * kPlane3;
+        const float* cur = smem + slot_c * kPlane3;
+        int rbeg = 0, rend = 0;
+        if (RECV) {  // receivers of this plane (Born / nonlinear sampling, adjoint injection)
+            const int rk = tile_xy * M.Nz + z;
+            rbeg = M.rec_ptr[rk];
+            rend = M.rec_ptr[rk + 1];
+        }
         if (MODE == STEP3_BORN || MODE == STEP3_INC_SAMPLE) {
             if (rend > rbeg) {
                 float* dout = M.data + (long long)shot * M.dss + (long long)b * M.dts + (long long)n * M.nr;
@@ -124,17 +177,20 @@ __global__ void __launch_bounds__(kThreads) k_step3d(const __grid_constant__ Ste
             __syncthreads();
         }
         if (col_ok && z < M.Nz) {
-            const long long off = ((long long)z * M.Ny + y) * M.P + x;
+            const long long off = off0 + (long long)iz * plane_stride;
             const float* rp = cur + (ly + 4) * kHX3 + lx + 4;
             const float4 a = ld4(rp - 4), c = ld4(rp), d = ld4(rp + 4);
+            // x taps in first-difference form (11 shared differences for the 4 cells)
             const float v[12] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
+            float dx[11];
+#pragma unroll
+            for (int i = 0; i < 11; ++i) dx[i] = v[i + 1] - v[i];
             float L[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float u0 = v[4 + j];
-                float acc = 0.f;
+                float acc = M.cxm[0] * (dx[4 + j] - dx[3 + j]);
 #pragma unroll
-                for (int k = 1; k <= 4; ++k) acc = fmaf(M.lx[k - 1], (v[4 + j + k] - u0) + (v[4 + j - k] - u0), acc);
+                for (int m = 1; m < 4; ++m) acc = fmaf(M.cxm[m], dx[4 + j + m] - dx[3 + j - m], acc);
                 L[j] = acc;
             }
 #pragma unroll
@@ -146,34 +202,35 @@ __global__ void __launch_bounds__(kThreads) k_step3d(const __grid_constant__ Ste
                 L[2] = fmaf(w, (up.z - c.z) + (dn.z - c.z), L[2]);
                 L[3] = fmaf(w, (up.w - c.w) + (dn.w - c.w), L[3]);
             }
+            const int cofs = (ly + 4) * kHX3 + lx + 4;
 #pragma unroll
             for (int k = 1; k <= 4; ++k) {
-                const float4 up = ld4(smem + ((iz + 4 - k) % kRing) * kPlane3 + (ly + 4) * kHX3 + lx + 4);
-                const float4 dn = ld4(smem + ((iz + 4 + k) % kRing) * kPlane3 + (ly + 4) * kHX3 + lx + 4);
+                int su = slot_c - k, sd = slot_c + k;
+                su += (su < 0) ? kRing : 0;
+                sd -= (sd >= kRing) ? kRing : 0;
+                const float4 up = ld4(smem + su * kPlane3 + cofs);
+                const float4 dn = ld4(smem + sd * kPlane3 + cofs);
                 const float w = M.lz[k - 1];
                 L[0] = fmaf(w, (up.x - c.x) + (dn.x - c.x), L[0]);
                 L[1] = fmaf(w, (up.y - c.y) + (dn.y - c.y), L[1]);
                 L[2] = fmaf(w, (up.z - c.z) + (dn.z - c.z), L[2]);
                 L[3] = fmaf(w, (up.w - c.w) + (dn.w - c.w), L[3]);
             }
-            const float4 sv = ld4(M.s + off);
-            const float4 ov = ld4(outv + off);
+            const float4 sv = cur_pw.s;
+            const float4 ov = cur_pw.prev;
             float src[4] = {0.f, 0.f, 0.f, 0.f};
             float Dv[4] = {0.f, 0.f, 0.f, 0.f};
             if (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) {
-                if (z == sz && y == sy) {
-                    const int j = sx - x;
-                    add_lane(src, j, fsrc);
-                }
+                if (z == sz && y == sy) add_lane(src, sx - x, fsrc);
             } else if (MODE == STEP3_BORN) {
-                const float4 dd = ld4(M.Din + (long long)shot * M.Din_shot_stride + off);
-                const float4 dmv = ld4(M.dm + (long long)b * F + off);
+                const float4 dd = cur_pw.d;
+                const float4 dmv = cur_pw.dm;
                 L[0] = __fmaf_rn(-dmv.x, dd.x, L[0]);  // Born source -dm Dtt u folded into L
                 L[1] = __fmaf_rn(-dmv.y, dd.y, L[1]);
                 L[2] = __fmaf_rn(-dmv.z, dd.z, L[2]);
                 L[3] = __fmaf_rn(-dmv.w, dd.w, L[3]);
             } else {
-                const float4 dd = ld4(M.Din + (long long)shot * M.Din_shot_stride + off);
+                const float4 dd = cur_pw.d;
                 Dv[0] = dd.x;
                 Dv[1] = dd.y;
                 Dv[2] = dd.z;
@@ -201,12 +258,12 @@ __global__ void __launch_bounds__(kThreads) k_step3d(const __grid_constant__ Ste
                 st4(M.Dout + (long long)shot * M.Dout_shot_stride + off, make_float4(Dw[0], Dw[1], Dw[2], Dw[3]));
             if (MODE == STEP3_ADJ) {
                 float* ip = M.img + (long long)(shot * M.nfield + b) * F + off;
-                float4 iv = ld4(ip);
+                float4 iv = cur_pw.img;
                 const float t0 = __fmul_rn(-Dv[0], o[0]), t1 = __fmul_rn(-Dv[1], o[1]);
                 const float t2 = __fmul_rn(-Dv[2], o[2]), t3 = __fmul_rn(-Dv[3], o[3]);
                 if (KAHAN) {
                     float* cp = M.comp + (long long)(shot * M.nfield + b) * F + off;
-                    float4 cv = ld4(cp);
+                    float4 cv = cur_pw.cmp;
                     kahan4(iv, cv, t0, t1, t2, t3);
                     st4(cp, cv);
                 } else {
@@ -222,11 +279,26 @@ __global__ void __launch_bounds__(kThreads) k_step3d(const __grid_constant__ Ste
         if (tid == 0) {
             const int k = iz + kRing;
             if (k < nplanes) {
-                mbar_expect_tx(&bars[k % kRing], kPlaneBytes3);
-                tma_load_4d(smem + (k % kRing) * kPlane3, &M.tm, x0 - 4, y0 - 4, z0 - 4 + k, vol_cur,
-                            &bars[k % kRing]);
+                int sf = slot_c - 4;  // slot of plane iz
+                sf += (sf < 0) ? kRing : 0;
+                mbar_expect_tx(&bars[sf], kPlaneBytes3);
+                tma_load_4d(smem + sf * kPlane3, &M.tm, x0 - 4, y0 - 4, z0 - 4 + k, vol_cur, &bars[sf]);
             }
         }
+        slot_c = (slot_c + 1 == kRing) ? 0 : slot_c + 1;
+        if (++slot_w == kRing) {
+            slot_w = 0;
+            ph_w ^= 1u;
+        }
+        return true;
+    };
+
+    // two planes per iteration: the operand bundles alternate roles instead of being copied
+    Pw3 pa, pb;
+    if (col_ok && nloc > 0) load_pw3<MODE, KAHAN>(M, outv, off0, shot, b, F, pa);
+    for (int iz = 0; iz < nloc; iz += 2) {
+        if (!plane(iz, pa, pb)) return;
+        if (iz + 1 < nloc && !plane(iz + 1, pb, pa)) return;
     }
 }
 

@@ -115,6 +115,8 @@ def ragged():
     {"pipeline": 2, "pipe_rows": 1, "shot_group": 2},
     {"pipeline": 3, "pipe_rows": 2, "shot_wave": 3},
     {"pipe_rows": 2, "shot_wave": 2, "shot_group": 1, "dtt_history": 1},
+    {"pipeline": 2, "pipe_rows": 1, "pipe_rows_adj": 2, "shot_group": 3},
+    {"pipeline": 3, "pipeline_adj": 0, "pipe_rows": 2, "shot_wave": 4},
     {"dtt_history": 1},
     {"dtt_history": 1, "pipeline": 0, "shot_wave": 2},
     {"use_graph": 1},
@@ -140,7 +142,9 @@ def test_kernel_variants_give_identical_bits(cuda_device, ragged):
     d0 = None
     outs = []
     for opts in [{"pipeline": 0}, {"pipeline": 2, "pipe_rows": 1}, {"pipeline": 3, "pipe_rows": 2},
-                 {"pipeline": 2, "pipe_rows": 2, "use_graph": 1}, {"pipeline": 3, "pipe_rows": 1, "dtt_history": 1}]:
+                 {"pipeline": 2, "pipe_rows": 2, "use_graph": 1}, {"pipeline": 3, "pipe_rows": 1, "dtt_history": 1},
+                 {"pipeline": 2, "pipe_rows": 1, "pipe_rows_adj": 2},
+                 {"pipeline": 2, "pipeline_adj": 0, "pipe_rows": 2}]:
         p = make_probe(wl)
         p.set_option("shot_group", 2)
         for k, v in opts.items():
