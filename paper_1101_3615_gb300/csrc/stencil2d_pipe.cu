@@ -209,9 +209,21 @@ __global__ void __launch_bounds__(kWsThreads, R == 1 ? 4 : 3) k_fwd2d_ws(const _
         if (lane != 0) return;
         int s = 0, g = 0;
         uint32_t eph = 0;  // phase of empty[s] to wait for (once the ring has wrapped)
+        // the next item is decoded one item ahead, so that its global lookups (receiver range,
+        // source cell, wavelet sample) overlap the waits of the current one
+        auto decode_fwd = [&](int it) {
+            Group d = decode<R>(p, it);
+            const ModelStep2D& Md = p.m[d.mi];
+            d.sz = Md.src_zx[2 * d.unit];
+            d.sx = Md.src_zx[2 * d.unit + 1];
+            d.fsrc = Md.wavelet[n] * Md.vol_inv;
+            return d;
+        };
+        Group qn = (blockIdx.x < total) ? decode_fwd(blockIdx.x) : Group{};
         for (int item = blockIdx.x;; item += gridDim.x) {
             const bool done = item >= total;
-            Group q = done ? Group{} : decode<R>(p, item);
+            Group q = qn;
+            if (!done && item + (int)gridDim.x < total) qn = decode_fwd(item + gridDim.x);
             const int ngr = done ? 1 : (KIND == FWD_BORN ? 1 + p.m[q.mi].nb : 1);
             for (int f = 0; f < ngr; ++f, ++g) {
                 if (g >= S && !mbar_wait_bounded(&empty[s], eph)) {
@@ -225,11 +237,6 @@ __global__ void __launch_bounds__(kWsThreads, R == 1 ? 4 : 3) k_fwd2d_ws(const _
                 }
                 const ModelStep2D& M = p.m[q.mi];
                 q.f = f;
-                if (f == 0) {
-                    q.sz = M.src_zx[2 * q.unit];
-                    q.sx = M.src_zx[2 * q.unit + 1];
-                    q.fsrc = M.wavelet[n] * M.vol_inv;
-                }  // later fields of the same item keep these values
                 info[s] = q;
                 float* st = smem + s * T::FWD_STAGE;
                 mbar_expect_tx(&full[s], T::HALO_B + 2 * T::PLAIN_B);
@@ -360,9 +367,11 @@ __global__ void __launch_bounds__(kWsThreads, (NBC * R >= 8) ? 1 : 2) k_adj2d_ws
     if (warp == kConsumerWarps) {  // ---------------- producer warp
         int s = 0, g = 0;
         uint32_t eph = 0;
+        Group qn = (blockIdx.x < total) ? decode<R>(p, blockIdx.x) : Group{};  // one item ahead
         for (int item = blockIdx.x;; item += gridDim.x) {
             const bool done = item >= total;
-            Group q = done ? Group{} : decode<R>(p, item);
+            Group q = qn;
+            if (!done && item + (int)gridDim.x < total) qn = decode<R>(p, item + gridDim.x);
             int nsh = 1, nbc = 1;
             if (!done) {
                 const ModelStep2D& M = p.m[q.mi];
