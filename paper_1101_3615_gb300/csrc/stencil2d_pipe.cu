@@ -83,12 +83,41 @@ __device__ __forceinline__ float cell_update(const ModelStep2D& M, bool fast, in
     return leapfrog(G, c, am, prev, rhs);
 }
 
+// Packed FP32x2 arithmetic on the lane pairs (0,1), (2,3) of a float4: each lane is rounded
+// exactly as the scalar operation of the same name, so packed and scalar paths agree bit for bit.
+struct P4 {
+    float2 a, b;
+};
+__device__ __forceinline__ P4 p4(const float4& v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ P4 p4(float v0, float v1, float v2, float v3) {
+    return {make_float2(v0, v1), make_float2(v2, v3)};
+}
+__device__ __forceinline__ float4 f4(const P4& p) { return make_float4(p.a.x, p.a.y, p.b.x, p.b.y); }
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) {  // x - y, one rounding
+    return __ffma2_rn(y, make_float2(-1.f, -1.f), x);
+}
+__device__ __forceinline__ P4 p4add(const P4& x, const P4& y) { return {__fadd2_rn(x.a, y.a), __fadd2_rn(x.b, y.b)}; }
+__device__ __forceinline__ P4 p4sub(const P4& x, const P4& y) { return {sub2(x.a, y.a), sub2(x.b, y.b)}; }
+__device__ __forceinline__ P4 p4mul(const P4& x, const P4& y) { return {__fmul2_rn(x.a, y.a), __fmul2_rn(x.b, y.b)}; }
+__device__ __forceinline__ P4 p4fma(const P4& x, const P4& y, const P4& z) {
+    return {__ffma2_rn(x.a, y.a, z.a), __ffma2_rn(x.b, y.b, z.b)};
+}
+__device__ __forceinline__ P4 p4neg(const P4& x) {
+    return {make_float2(-x.a.x, -x.a.y), make_float2(-x.b.x, -x.b.y)};
+}
+// leapfrog() of an interior cell (G = a- = 1): (2c - prev) + rhs; the factor G = 1 is exact.
+__device__ __forceinline__ P4 p4leap1(const P4& c, const P4& prev, const P4& rhs) {
+    return p4add(p4sub(p4add(c, c), prev), rhs);
+}
+
 // Laplacian of R rows x 4 cells whose first cell sits at halo coordinates (row, col).
 // Both axes in first-difference form: with d_i = v_{i+1} - v_i,
 //   sum_k w_k (v_{c+k} + v_{c-k} - 2 v_c) = sum_{m=0..3} C_m (d_{c+m} - d_{c-m-1}),
 //   C_m = sum_{k>m} w_k / h^2,
 // x first (11 shared differences per row), then z (R + 7 shared differences per column).
-template <int R>
+// PACKED: z taps in packed FP32x2 (the forward kernels) or scalar (the adjoint, where the packed
+// form measured slower); the two give the same bits.
+template <int R, bool PACKED>
 __device__ __forceinline__ void lap_rows(const float* t, int row, int col, const ModelStep2D& M, float4 c[R],
                                          float L[R][4]) {
     const float* rp = t + row * HX + col;
@@ -111,43 +140,91 @@ __device__ __forceinline__ void lap_rows(const float* t, int row, int col, const
     // z, outward: rows below the first cell row (lo) and above the last (hi) are loaded
     // as the tap index m grows; row r's term m is C_m ((v_{r+m+1} - v_{r+m}) - (v_{r-m} - v_{r-m-1})).
     // Differences between rows inside the block are formed once and shared by the R rows.
+    if (!PACKED) {
+        if (R == 1) {
+            float4 lo = c[0], hi = c[0];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const float4 dn = ld4(rp - (m + 1) * HX), up = ld4(rp + (m + 1) * HX);
+                L[0][0] = fmaf(M.czm[m], (up.x - hi.x) - (lo.x - dn.x), L[0][0]);
+                L[0][1] = fmaf(M.czm[m], (up.y - hi.y) - (lo.y - dn.y), L[0][1]);
+                L[0][2] = fmaf(M.czm[m], (up.z - hi.z) - (lo.z - dn.z), L[0][2]);
+                L[0][3] = fmaf(M.czm[m], (up.w - hi.w) - (lo.w - dn.w), L[0][3]);
+                lo = dn;
+                hi = up;
+            }
+        } else {
+            const float4 c0 = c[0], c1 = c[R - 1];
+            const float4 gin = make_float4(c1.x - c0.x, c1.y - c0.y, c1.z - c0.z, c1.w - c0.w);
+            float4 lo = c0, hi = c1, glo = gin, ghi = gin;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const float4 dn = ld4(rp - (m + 1) * HX), up = ld4(rp + (m + 2) * HX);
+                const float4 gd = make_float4(lo.x - dn.x, lo.y - dn.y, lo.z - dn.z, lo.w - dn.w);
+                const float4 gu = make_float4(up.x - hi.x, up.y - hi.y, up.z - hi.z, up.w - hi.w);
+                L[0][0] = fmaf(M.czm[m], ghi.x - gd.x, L[0][0]);
+                L[0][1] = fmaf(M.czm[m], ghi.y - gd.y, L[0][1]);
+                L[0][2] = fmaf(M.czm[m], ghi.z - gd.z, L[0][2]);
+                L[0][3] = fmaf(M.czm[m], ghi.w - gd.w, L[0][3]);
+                L[R - 1][0] = fmaf(M.czm[m], gu.x - glo.x, L[R - 1][0]);
+                L[R - 1][1] = fmaf(M.czm[m], gu.y - glo.y, L[R - 1][1]);
+                L[R - 1][2] = fmaf(M.czm[m], gu.z - glo.z, L[R - 1][2]);
+                L[R - 1][3] = fmaf(M.czm[m], gu.w - glo.w, L[R - 1][3]);
+                lo = dn;
+                hi = up;
+                glo = gd;
+                ghi = gu;
+            }
+        }
+        return;
+    }
+    // (packed: the same subtractions and fused multiply-adds, two lanes per instruction)
     if (R == 1) {
-        float4 lo = c[0], hi = c[0];
+        P4 acc = p4(L[0][0], L[0][1], L[0][2], L[0][3]);
+        P4 lo = p4(c[0]), hi = lo;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const float4 dn = ld4(rp - (m + 1) * HX), up = ld4(rp + (m + 1) * HX);
-            L[0][0] = fmaf(M.czm[m], (up.x - hi.x) - (lo.x - dn.x), L[0][0]);
-            L[0][1] = fmaf(M.czm[m], (up.y - hi.y) - (lo.y - dn.y), L[0][1]);
-            L[0][2] = fmaf(M.czm[m], (up.z - hi.z) - (lo.z - dn.z), L[0][2]);
-            L[0][3] = fmaf(M.czm[m], (up.w - hi.w) - (lo.w - dn.w), L[0][3]);
+            const P4 dn = p4(ld4(rp - (m + 1) * HX)), up = p4(ld4(rp + (m + 1) * HX));
+            const P4 w = p4(M.czm[m], M.czm[m], M.czm[m], M.czm[m]);
+            acc = p4fma(w, p4sub(p4sub(up, hi), p4sub(lo, dn)), acc);
             lo = dn;
             hi = up;
         }
+        const float4 o = f4(acc);
+        L[0][0] = o.x;
+        L[0][1] = o.y;
+        L[0][2] = o.z;
+        L[0][3] = o.w;
     } else {
         // R = 2: values v_{-4..5} relative to row 0; g_i = v_{i+1} - v_i.
         // row 0 term m: g_m - g_{-m-1}; row 1 term m: g_{m+1} - g_{-m}.
-        const float4 c0 = c[0], c1 = c[1];
-        float4 gin = make_float4(c1.x - c0.x, c1.y - c0.y, c1.z - c0.z, c1.w - c0.w);  // g_0
-        float4 lo = c0, hi = c1;        // current outermost rows below / above
-        float4 glo = gin, ghi = gin;    // g_{-m} (row 1's lower) and g_m (row 0's upper) of the last step
+        P4 a0 = p4(L[0][0], L[0][1], L[0][2], L[0][3]), a1 = p4(L[R - 1][0], L[R - 1][1], L[R - 1][2], L[R - 1][3]);
+        const P4 c0 = p4(c[0]), c1 = p4(c[R - 1]);
+        const P4 gin = p4sub(c1, c0);  // g_0
+        P4 lo = c0, hi = c1;           // current outermost rows below / above
+        P4 glo = gin, ghi = gin;       // g_{-m} (row 1's lower) and g_m (row 0's upper) of the last step
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const float4 dn = ld4(rp - (m + 1) * HX), up = ld4(rp + (m + 2) * HX);
-            const float4 gd = make_float4(lo.x - dn.x, lo.y - dn.y, lo.z - dn.z, lo.w - dn.w);  // g_{-m-1}
-            const float4 gu = make_float4(up.x - hi.x, up.y - hi.y, up.z - hi.z, up.w - hi.w);  // g_{m+1}
-            L[0][0] = fmaf(M.czm[m], ghi.x - gd.x, L[0][0]);
-            L[0][1] = fmaf(M.czm[m], ghi.y - gd.y, L[0][1]);
-            L[0][2] = fmaf(M.czm[m], ghi.z - gd.z, L[0][2]);
-            L[0][3] = fmaf(M.czm[m], ghi.w - gd.w, L[0][3]);
-            L[R - 1][0] = fmaf(M.czm[m], gu.x - glo.x, L[R - 1][0]);
-            L[R - 1][1] = fmaf(M.czm[m], gu.y - glo.y, L[R - 1][1]);
-            L[R - 1][2] = fmaf(M.czm[m], gu.z - glo.z, L[R - 1][2]);
-            L[R - 1][3] = fmaf(M.czm[m], gu.w - glo.w, L[R - 1][3]);
+            const P4 dn = p4(ld4(rp - (m + 1) * HX)), up = p4(ld4(rp + (m + 2) * HX));
+            const P4 gd = p4sub(lo, dn);  // g_{-m-1}
+            const P4 gu = p4sub(up, hi);  // g_{m+1}
+            const P4 w = p4(M.czm[m], M.czm[m], M.czm[m], M.czm[m]);
+            a0 = p4fma(w, p4sub(ghi, gd), a0);
+            a1 = p4fma(w, p4sub(gu, glo), a1);
             lo = dn;
             hi = up;
             glo = gd;
             ghi = gu;
         }
+        const float4 o0 = f4(a0), o1 = f4(a1);
+        L[0][0] = o0.x;
+        L[0][1] = o0.y;
+        L[0][2] = o0.z;
+        L[0][3] = o0.w;
+        L[R - 1][0] = o1.x;
+        L[R - 1][1] = o1.y;
+        L[R - 1][2] = o1.z;
+        L[R - 1][3] = o1.w;
     }
 }
 
@@ -285,7 +362,7 @@ __global__ void __launch_bounds__(kWsThreads, R == 1 ? 4 : 3) k_fwd2d_ws(const _
         const bool fast = q.fast != 0;
         float L[R][4];
         float4 c[R];
-        lap_rows<R>(st, lz + 4, lx + 4, M, c, L);
+        lap_rows<R, true>(st, lz + 4, lx + 4, M, c, L);
         if (q.f == 0) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -294,11 +371,19 @@ __global__ void __launch_bounds__(kWsThreads, R == 1 ? 4 : 3) k_fwd2d_ws(const _
                 const float4 pold = ld4(st + T::HALO + T::PLAIN + (lz + r) * kTX + lx);
                 if (z == q.sz) add_lane(L[r], q.sx - x, q.fsrc);
                 float o[4];
+                if (fast) {
+                    const P4 Fo = p4mul(p4(sv[r]), p4(L[r][0], L[r][1], L[r][2], L[r][3]));
+                    const float4 Dv = f4(p4mul(Fo, p4(M.inv_dt2, M.inv_dt2, M.inv_dt2, M.inv_dt2)));
+                    const float4 ov = f4(p4leap1(p4(c[r]), p4(pold), Fo));
+                    D[r][0] = Dv.x, D[r][1] = Dv.y, D[r][2] = Dv.z, D[r][3] = Dv.w;
+                    o[0] = ov.x, o[1] = ov.y, o[2] = ov.z, o[3] = ov.w;
+                } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float Fo = __fmul_rn(get(sv[r], j), L[r][j]);
-                    D[r][j] = __fmul_rn(Fo, M.inv_dt2);
-                    o[j] = cell_update(M, fast, z, x + j, get(c[r], j), get(pold, j), Fo);
+                    for (int j = 0; j < 4; ++j) {
+                        const float Fo = __fmul_rn(get(sv[r], j), L[r][j]);
+                        D[r][j] = __fmul_rn(Fo, M.inv_dt2);
+                        o[j] = cell_update(M, false, z, x + j, get(c[r], j), get(pold, j), Fo);
+                    }
                 }
                 if (fast || (z < M.Nz && x < M.Nx)) {
                     const long long off = (long long)z * M.P + x;
@@ -318,10 +403,17 @@ __global__ void __launch_bounds__(kWsThreads, R == 1 ? 4 : 3) k_fwd2d_ws(const _
                 const float4 dmv = ld4(st + T::HALO + (lz + r) * kTX + lx);
                 const float4 fo = ld4(st + T::HALO + T::PLAIN + (lz + r) * kTX + lx);
                 float o[4];
+                if (fast) {
+                    const P4 src = p4fma(p4neg(p4(dmv)), p4(D[r][0], D[r][1], D[r][2], D[r][3]),
+                                         p4(L[r][0], L[r][1], L[r][2], L[r][3]));
+                    const float4 ov = f4(p4leap1(p4(c[r]), p4(fo), p4mul(p4(sv[r]), src)));
+                    o[0] = ov.x, o[1] = ov.y, o[2] = ov.z, o[3] = ov.w;
+                } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float src = __fmaf_rn(-get(dmv, j), D[r][j], L[r][j]);
-                    o[j] = cell_update(M, fast, z, x + j, get(c[r], j), get(fo, j), __fmul_rn(get(sv[r], j), src));
+                    for (int j = 0; j < 4; ++j) {
+                        const float src = __fmaf_rn(-get(dmv, j), D[r][j], L[r][j]);
+                        o[j] = cell_update(M, false, z, x + j, get(c[r], j), get(fo, j), __fmul_rn(get(sv[r], j), src));
+                    }
                 }
                 if (fast || (z < M.Nz && x < M.Nx))
                     st4(M.f + (long long)((shot * M.nb + b) * 2 + po) * M.F + (long long)z * M.P + x,
@@ -481,7 +573,7 @@ __global__ void __launch_bounds__(kWsThreads, (NBC * R >= 8) ? 1 : 2) k_adj2d_ws
         }
         float L[R][4];
         float4 c[R];
-        lap_rows<R>(st, lz + 4, lx + 4, M, c, L);
+        lap_rows<R, false>(st, lz + 4, lx + 4, M, c, L);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int z = q.z0 + lz + r;
