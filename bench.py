@@ -86,6 +86,10 @@ def profile_run(a, wl):
         p.set_option("pipeline", a.pipeline)
         if a.pipe_rows:
             p.set_option("pipe_rows", a.pipe_rows)
+    if a.fixed:                       # pf,pa,R,G as in the timed runs
+        pf, pa, rows, grp = (int(v) for v in a.fixed.split(","))
+        for k, v in (("pipeline", pf), ("pipeline_adj", pa), ("pipe_rows", rows), ("shot_group", grp)):
+            p.set_option(k, v)
     dm = torch.tensor(wl.trials, device=dev)
     if a.profile == "fwd":
         run = lambda: p.apply_F(dm)

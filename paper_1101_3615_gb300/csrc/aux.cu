@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -141,6 +143,44 @@ __global__ void k_sample(const float* __restrict__ field, long long pss, long lo
         const float v = field[s * pss + b * pst + (long long)plane * F + cell];
         data[s * dss + b * dst_ + (long long)n * nr + r] = v;
     }
+}
+
+// Adjoint receiver injection R^T r^n for `nsteps` time levels, scattered into the compact
+// band buffer (the grid rows that hold receivers): one thread per (receiver cell, step, shot,
+// trial) sums that cell's receivers in their list order (no atomics, so the result is the
+// same on every run) and stores it at band * P + x of its (slot, shot, trial) block.  Slot
+// k holds time level n_hi - k.  Cells without receivers stay as the caller zeroed them.
+__global__ void k_build_injection(const float* __restrict__ rdata, long long dss, long long dts, int nr,
+                                  int n_hi, int nsteps, int nshots, int nb, int nuc,
+                                  const int* __restrict__ uc_ptr, const int* __restrict__ uc_rec,
+                                  const int* __restrict__ uc_pos, float* __restrict__ inj, long long block) {
+    const long long total = (long long)nuc * nsteps * nshots * nb;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % nuc);
+        long long r = i / nuc;
+        const int b = (int)(r % nb);
+        r /= nb;
+        const int s = (int)(r % nshots);
+        const int k = (int)(r / nshots);
+        const int n = n_hi - k;
+        const float* row = rdata + s * dss + b * dts + (long long)n * nr;
+        float v = 0.f;
+        for (int q = uc_ptr[c]; q < uc_ptr[c + 1]; ++q) v += row[uc_rec[q]];
+        inj[(((long long)k * nshots + s) * nb + b) * block + uc_pos[c]] = v;
+    }
+}
+
+cudaError_t launch_build_injection(const float* rdata, long long dss, long long dts, int nr, int n_hi, int nsteps,
+                                   int nshots, int nb, int nuc, const int* uc_ptr, const int* uc_rec,
+                                   const int* uc_pos, float* inj, long long block, cudaStream_t st) {
+    const long long total = (long long)nuc * nsteps * nshots * nb;
+    if (total <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (int)std::min<long long>((total + threads - 1) / threads, 65535);
+    k_build_injection<<<blocks, threads, 0, st>>>(rdata, dss, dts, nr, n_hi, nsteps, nshots, nb, nuc, uc_ptr, uc_rec,
+                                                   uc_pos, inj, block);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sample(const float* field, long long plane_stride_shot,

@@ -123,6 +123,9 @@ __device__ __forceinline__ float get(const float4& v, int j) {
     return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
 
+// Bring the line holding p into L2 (a hint: no registers held, nothing returned).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Kahan-compensated s += v with running compensation c (explicit roundings).
 __device__ __forceinline__ void kahan1(float& s, float& c, float v) {
     const float y = __fsub_rn(v, c);

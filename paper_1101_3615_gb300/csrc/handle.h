@@ -36,6 +36,7 @@ struct Workspace {
     float* comp = nullptr;
     float* s_tmp = nullptr;   // [F]
     int* src_wave = nullptr;  // [W][2] padded sources of the wave
+    float* inj = nullptr;     // [K][W][nb][nband][P] adjoint injection of one segment (2D)
     CUtensorMap tm_u, tm_f;
     // pipelined kernels: halo and plain boxes for tiles of 64 x 16 rows, one set for the
     // forward kernels and one for the adjoint (their row counts are chosen separately)
@@ -90,6 +91,13 @@ struct probe_s {
     // receivers by pipelined-kernel tile (64 x 16R), R = 1, 2
     int* d_wrec_ptr[3] = {nullptr, nullptr, nullptr};
     int* d_wrec_idx[3] = {nullptr, nullptr, nullptr};
+    // 2D adjoint injection: grid rows holding receivers ("bands") and the receiver cells with
+    // their receivers (CSR, receiver order), built once per handle
+    int* d_rrow = nullptr;       // [Nz] band index or -1
+    int* d_uc_ptr = nullptr;     // [nuc + 1]
+    int* d_uc_rec = nullptr;     // [nr]
+    int* d_uc_pos = nullptr;     // [nuc] band * P + x
+    int nband = 0, nuc = 0;
     int ws_rows = 2;             // rows per thread R of the pipelined forward kernels
     int ws_rows_adj = 1;         // and of the pipelined adjoint kernels
     int* d_err = nullptr;

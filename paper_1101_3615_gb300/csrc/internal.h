@@ -45,6 +45,12 @@ struct alignas(128) ModelStep2D {
     int ws_tiles_z, ws_ntiles;   // their tile grid
     const int* ws_rec_ptr;       // receivers by pipelined tile (CSR over ws_ntiles)
     const int* ws_rec_idx;
+    // adjoint injection R^T r^n, prebuilt per checkpoint segment: rows that hold receivers
+    // ("bands") of each (slot, shot, trial), nband x P floats per block
+    const int* rrow;             // [Nz] band of a grid row, -1 without receivers
+    const float* inj;            // [slots][nshots][nb][nband][P]
+    int inj_slot;                // slot of this step
+    int nband;
     int block_begin;   // first grid.z index of this model in the launch
     int item_begin;    // pipelined kernels: first work item of this model
     int dtt_slots;     // Dtt planes per shot in the segment buffer
@@ -172,6 +178,9 @@ cudaError_t launch_sample(const float* field, long long plane_stride_shot,
                           long long data_shot_stride, long long data_trial_stride, int n,
                           cudaStream_t st);
 cudaError_t launch_check_finite(const float* a, long long n, int* err, cudaStream_t st);
+cudaError_t launch_build_injection(const float* rdata, long long dss, long long dts, int nr, int n_hi, int nsteps,
+                                   int nshots, int nb, int nuc, const int* uc_ptr, const int* uc_rec,
+                                   const int* uc_pos, float* inj, long long block, cudaStream_t st);
 // pc = plane parity of u^n (u^{n-1} is in the other plane of each shot).
 cudaError_t launch_encode_ckpt(const float* state, int nplanes, long long F, int pc, void* dst,
                                float* scales, int dtype, float* absmax_scratch, cudaStream_t st);

@@ -141,7 +141,7 @@ std::atomic<long long> g_generation{0};
 
 void free_ws(Workspace& w) {
     void* ptrs[] = {w.u, w.f, w.dm, w.data, w.ckpt, w.scales, w.absmax, w.dtt, w.img, w.comp, w.s_tmp,
-                    w.src_wave};
+                    w.src_wave, w.inj};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Workspace();
@@ -239,6 +239,8 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     TRY(alloc((void**)&w.comp, (size_t)G * std::max(nb, 1) * F * 4));
     TRY(alloc((void**)&w.s_tmp, (size_t)F * 4));
     TRY(alloc((void**)&w.src_wave, (size_t)W * 3 * 4));
+    if (with_ckpt && h->ndim == 2 && h->nband > 0)  // one segment of adjoint injection
+        TRY(alloc((void**)&w.inj, (size_t)h->K * W * std::max(nb, 1) * h->nband * h->P * 4));
     // field planes must read as zero outside what the kernels write
     CK(h, cudaMemset(w.u, 0, (size_t)W * 2 * F * 4));
     CK(h, cudaMemset(w.f, 0, (size_t)W * std::max(nb, 1) * 2 * F * 4));
@@ -277,6 +279,40 @@ probe_status upload_csr(probe_t h, const std::vector<int>& key, int nkeys, int**
     return PROBE_OK;
 }
 
+// 2D adjoint injection layout: the grid rows that hold receivers (bands) and the distinct
+// receiver cells with their receivers in receiver order (so sums are formed in a fixed order).
+probe_status build_bands(probe_t h) {
+    std::vector<int> rrow(h->Nz, -1);
+    int nband = 0;
+    for (int r = 0; r < h->nr; ++r) {
+        const int z = h->rec_pad[2 * r];
+        if (rrow[z] < 0) rrow[z] = 0;
+    }
+    for (int z = 0; z < h->Nz; ++z)
+        if (rrow[z] == 0) rrow[z] = nband++;
+    std::map<std::pair<int, int>, std::vector<int>> cells;  // (band, x) -> receivers
+    for (int r = 0; r < h->nr; ++r)
+        cells[{rrow[h->rec_pad[2 * r]], h->rec_pad[2 * r + 1]}].push_back(r);
+    std::vector<int> ptr(1, 0), rec, pos;
+    for (const auto& kv : cells) {
+        for (int r : kv.second) rec.push_back(r);
+        ptr.push_back((int)rec.size());
+        pos.push_back(kv.first.first * h->P + kv.first.second);
+    }
+    auto upload = [&](int** dst, const std::vector<int>& v) -> probe_status {
+        CK(h, cudaMalloc(dst, std::max<size_t>(v.size(), 1) * 4));
+        if (!v.empty()) CK(h, cudaMemcpy(*dst, v.data(), v.size() * 4, cudaMemcpyHostToDevice));
+        return PROBE_OK;
+    };
+    TRY(upload(&h->d_rrow, rrow));
+    TRY(upload(&h->d_uc_ptr, ptr));
+    TRY(upload(&h->d_uc_rec, rec));
+    TRY(upload(&h->d_uc_pos, pos));
+    h->nband = nband;
+    h->nuc = (int)pos.size();
+    return PROBE_OK;
+}
+
 // Receivers grouped by 2D tile (CSR) for the in-tile sampling and injection.
 probe_status build_rec_tiles(probe_t h) {
     std::vector<int> key(h->nr);
@@ -302,6 +338,7 @@ probe_status build_rec_tiles(probe_t h) {
         }
     }
     TRY(upload_csr(h, key, nkeys, &h->d_rec_tile_ptr, &h->d_rec_tile_idx));
+    if (h->ndim == 2 && !h->d_rrow) TRY(build_bands(h));
     if (h->ndim == 2) {
         for (int R = 1; R <= 2; ++R) {  // tiles of the pipelined kernels (64 x 16R)
             const int tz = (h->Nz + 16 * R - 1) / (16 * R);
@@ -356,6 +393,10 @@ void fill_model(const Job& jb, ModelStep2D& m, const WsMaps& maps, int* blocks_f
     m.ws_ntiles = m.ws_tiles_z * h->tiles_x;
     m.ws_rec_ptr = h->d_wrec_ptr[R];
     m.ws_rec_idx = h->d_wrec_idx[R];
+    m.rrow = h->d_rrow;
+    m.inj = w.inj;
+    m.nband = h->nband;
+    m.inj_slot = 0;
     if (encode_plain(h, &m.tm_sp, jb.s, 1, 16 * R) != PROBE_OK) m.s = nullptr;
     m.Nz = h->Nz;
     m.Nx = h->Nx;
@@ -421,6 +462,7 @@ struct Sweep {
     int tile_z = 16;
     int pipeline = 0;      // forward: 0 one tile per CTA; 2..4 persistent pipelined kernels
     int pipeline_adj = 0;  // adjoint variant
+    int inj_hi = -1;       // time level of injection slot 0 of the current segment (-1: slot 0)
     bool kahan = true;
     cudaStream_t st = nullptr;
     int nt = 0, K = 0, nck = 0;
@@ -502,7 +544,10 @@ probe_status launch_fwd_step(Sweep& sw, FwdKind kind, int n, int slot) {
 probe_status launch_adj_step(Sweep& sw, int n, int slot) {
     set_grid(sw, true);
     sw.pa.n = n;
-    for (int k = 0; k < sw.pa.nmodels; ++k) sw.pa.m[k].dtt_slot = slot;
+    for (int k = 0; k < sw.pa.nmodels; ++k) {
+        sw.pa.m[k].dtt_slot = slot;
+        sw.pa.m[k].inj_slot = sw.inj_hi >= 0 ? sw.inj_hi - n : 0;
+    }
     cudaError_t e = (sw.pipeline_adj && sw.tile_z == kPipeTZ)
                         ? launch_adj2d_pipe(sw.nbc, sw.kahan, sw.pipeline_adj, sw.pa, sw.chunks, sw.st)
                         : launch_adj2d(sw.tile_z, sw.nbc, sw.kahan, sw.pa, sw.blocks_adj, sw.chunks, sw.st);
@@ -567,6 +612,25 @@ probe_status run_forward(Sweep& sw, FwdKind kind, bool ckpt) {
 }
 
 // Adjoint sweep with segment-wise recomputation; accumulates into the images.
+// Receiver injection R^T r^n of time levels n_hi down to n_lo for every model of the sweep,
+// into the segment buffer (slot k = level n_hi - k); the adjoint steps read it.
+probe_status build_injection(Sweep& sw, int n_hi, int n_lo) {
+    for (Job& jb : sw.jobs) {
+        probe_t h = jb.h;
+        Workspace& w = h->ws;
+        if (!w.inj || h->nband == 0) continue;
+        const long long block = (long long)h->nband * h->P;
+        const int nb = std::max(jb.nb, 1);
+        CK(h, cudaMemsetAsync(w.inj, 0, (size_t)(n_hi - n_lo + 1) * jb.W * nb * block * 4, sw.st));
+        cudaError_t e = launch_build_injection(jb.rdata, jb.dss, jb.dts, h->nr, n_hi, n_hi - n_lo + 1, jb.W, nb,
+                                               h->nuc, h->d_uc_ptr, h->d_uc_rec, h->d_uc_pos, w.inj, block, sw.st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "receiver injection");
+        sw.launches_other++;
+    }
+    sw.inj_hi = n_hi;
+    return PROBE_OK;
+}
+
 probe_status run_adjoint(Sweep& sw) {
     for (Job& jb : sw.jobs) {
         Workspace& w = jb.h->ws;
@@ -577,9 +641,13 @@ probe_status run_adjoint(Sweep& sw) {
     if (h0->ws.history) {  // Dtt u^n kept for every step: no recomputation
         record(h0, ev++, sw.st);
         record(h0, ev++, sw.st);
-        for (int n = sw.nt - 1; n >= 1; --n) {
-            TRY(launch_adj_step(sw, n, n - 1));
-            sw.launches_adj += sw.chunks;
+        for (int n_hi = sw.nt - 1; n_hi >= 1; n_hi -= sw.K) {  // injection built K levels at a time
+            const int n_lo = std::max(1, n_hi - sw.K + 1);
+            TRY(build_injection(sw, n_hi, n_lo));
+            for (int n = n_hi; n >= n_lo; --n) {
+                TRY(launch_adj_step(sw, n, n - 1));
+                sw.launches_adj += sw.chunks;
+            }
         }
         record(h0, ev++, sw.st);
         return PROBE_OK;
@@ -603,6 +671,7 @@ probe_status run_adjoint(Sweep& sw) {
             sw.launches_rec++;
         }
         record(h0, ev++, sw.st);
+        TRY(build_injection(sw, k1, k0 + 1));
         for (int n = k1; n >= k0 + 1; --n) {
             TRY(launch_adj_step(sw, n, n - 1 - k0));
             sw.launches_adj += sw.chunks;
@@ -1062,6 +1131,7 @@ extern "C" void probe_destroy(probe_t h) {
     free_ws(h->ws);
     void* ptrs[] = {h->d_m0, h->d_s0, h->d_wavelet, h->d_src, h->d_rec, h->d_rec_tile_ptr, h->d_rec_tile_idx,
                     h->d_wrec_ptr[1], h->d_wrec_idx[1], h->d_wrec_ptr[2], h->d_wrec_idx[2],
+                    h->d_rrow, h->d_uc_ptr, h->d_uc_rec, h->d_uc_pos,
                     h->d_err, h->stage_in.p, h->stage_out.p};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -297,7 +297,6 @@ __global__ void __launch_bounds__(kThreads, (NBC * TZ <= 32) ? 4 : 2) k_adj2d(co
     const int nsh = min(M.shot_group, M.nshots - j0);
     const int niter = nsh * nbc;
     float* sbuf[2] = {smem, smem + T::FLOATS};
-    float* sinj = smem + 2 * T::FLOATS;  // TZ x 64 receiver injection
 
     const int rbeg = M.rec_tile_ptr[tile], rend = M.rec_tile_ptr[tile + 1];
     const bool has_rec = rend > rbeg;
@@ -354,20 +353,43 @@ __global__ void __launch_bounds__(kThreads, (NBC * TZ <= 32) ? 4 : 2) k_adj2d(co
                     tma_load_3d(sbuf[buf ^ 1], &M.tm_f, x0 - 4, z0 - 4, ((jn * nb + bn) * 2) + pc,
                                 &bars[buf ^ 1]);
                 }
-                float* fb = M.f + (long long)((shot * nb + b) * 2) * F;
-                float4 mo[ROWS];
+                // operands of the next iteration (its mu^{n+2}, a new shot's Dtt) or, on the last
+                // one, the image tiles: into L2 while this iteration computes
+                if (it + 1 < niter) {
+                    const int jn = j0 + (it + 1) / nbc, bn = b0 + (it + 1) % nbc;
+                    const float* fn = M.f + (long long)((jn * nb + bn) * 2 + po) * F;
+                    const float* dn = M.dtt + (long long)jn * M.dtt_shot_stride + (long long)M.dtt_slot * F;
 #pragma unroll
-                for (int r = 0; r < ROWS; ++r)
+                    for (int r = 0; r < ROWS; ++r) {
+                        if (!valid[r]) continue;
+                        prefetch_l2(fn + off[r]);
+                        if ((it + 1) % nbc == 0) prefetch_l2(dn + off[r]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NBC; ++k) {
+                        if (k >= nbc) continue;
+                        const long long boff = (long long)grp * M.img_group_stride + (long long)(b0 + k) * F;
+#pragma unroll
+                        for (int r = 0; r < ROWS; ++r) {
+                            if (!valid[r]) continue;
+                            prefetch_l2(M.img + boff + off[r]);
+                            if (KAHAN) prefetch_l2(M.comp + boff + off[r]);
+                        }
+                    }
+                }
+                float* fb = M.f + (long long)((shot * nb + b) * 2) * F;
+                float4 mo[ROWS], inj[ROWS];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
                     mo[r] = valid[r] ? ld4(fb + po * F + off[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                if (has_rec) {
-                    for (int i = tid; i < TZ * kTX; i += kThreads) sinj[i] = 0.f;
-                    __syncthreads();
-                    const float* rr = M.rdata + (long long)shot * M.data_shot_stride +
-                                      (long long)b * M.data_trial_stride + (long long)n * M.nr;
-                    for (int i = rbeg + tid; i < rend; i += kThreads) {
-                        const int rcv = M.rec_tile_idx[i];
-                        atomicAdd(&sinj[(M.rec_zx[2 * rcv] - z0) * kTX + (M.rec_zx[2 * rcv + 1] - x0)],
-                                  rr[rcv]);
+                    // receiver injection R^T r^n, prebuilt for this segment (rows with receivers only)
+                    inj[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (has_rec && valid[r]) {
+                        const int band = M.rrow[z0 + lz + 16 * r];
+                        if (band >= 0)
+                            inj[r] = ld4(M.inj + (((long long)M.inj_slot * M.nshots + shot) * nb + b) *
+                                                     ((long long)M.nband * M.P) + (long long)band * M.P + x);
                     }
                 }
                 const bool ok = mbar_wait_bounded(&bars[buf], (it >> 1) & 1);
@@ -383,11 +405,10 @@ __global__ void __launch_bounds__(kThreads, (NBC * TZ <= 32) ? 4 : 2) k_adj2d(co
                     float4 c;
                     lap4<HX>(sf, lz + 16 * r + 4, lx + 4, M, c, L);
                     if (has_rec) {
-                        const float4 iv = ld4(sinj + (lz + 16 * r) * kTX + lx);
-                        L[0] += iv.x;
-                        L[1] += iv.y;
-                        L[2] += iv.z;
-                        L[3] += iv.w;
+                        L[0] += inj[r].x;
+                        L[1] += inj[r].y;
+                        L[2] += inj[r].z;
+                        L[3] += inj[r].w;
                     }
                     float o[4];
                     const int z = z0 + lz + 16 * r;
@@ -441,7 +462,7 @@ size_t fwd2d_smem_bytes(FwdKind kind, int tile_z) {
 
 size_t adj2d_smem_bytes(int tile_z) {
     const size_t tile = (size_t)(kTX + 8) * (tile_z + 8) * 4;
-    return 2 * tile + (size_t)tile_z * kTX * 4;
+    return 2 * tile;  // double-buffered halo tiles
 }
 
 template <int TZ>

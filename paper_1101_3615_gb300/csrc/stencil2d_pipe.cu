@@ -42,8 +42,8 @@ struct Ws {
     static constexpr int HALO = HX * HZ;    // floats
     static constexpr int PLAIN = kTX * TZ;  // floats
     static constexpr int FWD_STAGE = HALO + 2 * PLAIN;
-    // adjoint stage: halo of mu^{n+1}, mu^{n+2}, Dtt, s, then either the injection tile or the
-    // image and compensation tiles of a trial's last group (a receiver tile reads its image from HBM)
+    // adjoint stage: halo of mu^{n+1}, mu^{n+2}, Dtt, s, and the image and compensation tiles of
+    // a trial's last group
     static constexpr int ADJ_STAGE = HALO + 5 * PLAIN;
     static constexpr unsigned HALO_B = HALO * 4u, PLAIN_B = PLAIN * 4u;
 };
@@ -489,19 +489,7 @@ __global__ void __launch_bounds__(kWsThreads, (NBC * R >= 8) ? 1 : 2) k_adj2d_ws
                     float* st = smem + s * T::ADJ_STAGE;
                     const int shot = q.unit * M.shot_group + jj;
                     const int b = M.chunk * NBC + bi;
-                    const bool inj = q.rend > q.rbeg;
-                    if (inj) {  // R^T r^n of this tile, assembled by the producer warp
-                        float* it = st + T::HALO + 3 * T::PLAIN;
-                        for (int i = lane; i < T::PLAIN / 4; i += 32) st4(it + 4 * i, make_float4(0.f, 0.f, 0.f, 0.f));
-                        __syncwarp();
-                        const float* rr = M.rdata + (long long)shot * M.data_shot_stride +
-                                          (long long)b * M.data_trial_stride + (long long)n * M.nr;
-                        for (int i = q.rbeg + lane; i < q.rend; i += 32) {
-                            const int rcv = M.ws_rec_idx[i];
-                            atomicAdd(&it[(M.rec_zx[2 * rcv] - q.z0) * kTX + (M.rec_zx[2 * rcv + 1] - q.x0)], rr[rcv]);
-                        }
-                        __syncwarp();
-                    }
+                    const bool inj = q.rend > q.rbeg;  // the consumers add the prebuilt R^T r^n
                     if (lane == 0) {
                         Group gi = q;
                         gi.f = jj * NBC + bi;
@@ -509,7 +497,7 @@ __global__ void __launch_bounds__(kWsThreads, (NBC * R >= 8) ? 1 : 2) k_adj2d_ws
                         gi.inj = inj;
                         info[s] = gi;
                         const int pl = (shot * M.nb + b) * 2;
-                        const bool with_d = bi == 0, with_s = (jj == 0) && (bi == 0), with_i = gi.last && !inj;
+                        const bool with_d = bi == 0, with_s = (jj == 0) && (bi == 0), with_i = gi.last;
                         mbar_expect_tx(&full[s], T::HALO_B + T::PLAIN_B + (with_d ? T::PLAIN_B : 0u) +
                                                      (with_s ? T::PLAIN_B : 0u) +
                                                      (with_i ? (KAHAN ? 2u : 1u) * T::PLAIN_B : 0u));
@@ -578,12 +566,16 @@ __global__ void __launch_bounds__(kWsThreads, (NBC * R >= 8) ? 1 : 2) k_adj2d_ws
         for (int r = 0; r < R; ++r) {
             const int z = q.z0 + lz + r;
             const float4 mo = ld4(st + T::HALO + (lz + r) * kTX + lx);
-            if (q.inj) {
-                const float4 in = ld4(st + T::HALO + 3 * T::PLAIN + (lz + r) * kTX + lx);
-                L[r][0] += in.x;
-                L[r][1] += in.y;
-                L[r][2] += in.z;
-                L[r][3] += in.w;
+            if (q.inj && z < M.Nz && x < M.Nx) {  // receiver injection R^T r^n, prebuilt for the segment
+                const int band = M.rrow[z];
+                if (band >= 0) {
+                    const float4 in = ld4(M.inj + (((long long)M.inj_slot * M.nshots + shot) * M.nb + b) *
+                                                      ((long long)M.nband * M.P) + (long long)band * M.P + x);
+                    L[r][0] += in.x;
+                    L[r][1] += in.y;
+                    L[r][2] += in.z;
+                    L[r][3] += in.w;
+                }
             }
             float o[4];
 #pragma unroll
@@ -611,9 +603,9 @@ __global__ void __launch_bounds__(kWsThreads, (NBC * R >= 8) ? 1 : 2) k_adj2d_ws
                         if (fast || (z < M.Nz && x < M.Nx)) {
                             const long long off = (long long)z * M.P + x;
                             const float* ist = st + T::HALO + 3 * T::PLAIN + (lz + r) * kTX + lx;
-                            float4 iv = q.inj ? ld4(img + off) : ld4(ist);
+                            float4 iv = ld4(ist);
                             if (KAHAN) {
-                                float4 cv = q.inj ? ld4(cmp + off) : ld4(ist + T::PLAIN);
+                                float4 cv = ld4(ist + T::PLAIN);
                                 kahan4(iv, cv, acc[k][r][0], acc[k][r][1], acc[k][r][2], acc[k][r][3]);
                                 st4(cmp + off, cv);
                             } else {

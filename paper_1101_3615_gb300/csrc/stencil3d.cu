@@ -55,8 +55,6 @@ __device__ __forceinline__ void load_pw3(const ModelStep3D& M, const float* outv
     }
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
 // The same operands two planes ahead, brought into L2 only (no registers held).
 template <int MODE, bool KAHAN>
 __device__ __forceinline__ void prefetch_pw3(const ModelStep3D& M, const float* outv, long long off, int shot, int b,
