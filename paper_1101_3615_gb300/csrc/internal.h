@@ -141,7 +141,8 @@ struct StepParams3D {
     ModelStep3D m;
 };
 
-cudaError_t launch_step3d(int mode, bool kahan, const StepParams3D& p, cudaStream_t st);
+// pipelined: the producer-warp variant for the forward modes (the adjoint always uses k_step3d)
+cudaError_t launch_step3d(int mode, bool kahan, bool pipelined, const StepParams3D& p, cudaStream_t st);
 size_t step3d_smem_bytes();
 
 // Launchers (stencil2d.cu).  `zblocks` = grid.z extent: shots (forward) or shot

@@ -742,7 +742,7 @@ struct Count3 {
 
 probe_status launch3(probe_t h, int mode, StepParams3D& p, int n, cudaStream_t st, const char* what) {
     p.n = n;
-    cudaError_t e = launch_step3d(mode, h->kahan != 0, p, st);
+    cudaError_t e = launch_step3d(mode, h->kahan != 0, h->opt_pipeline != 0, p, st);
     if (e != cudaSuccess) return cuda_fail(h, e, what);
     return PROBE_OK;
 }

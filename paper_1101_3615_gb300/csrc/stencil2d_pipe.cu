@@ -83,33 +83,6 @@ __device__ __forceinline__ float cell_update(const ModelStep2D& M, bool fast, in
     return leapfrog(G, c, am, prev, rhs);
 }
 
-// Packed FP32x2 arithmetic on the lane pairs (0,1), (2,3) of a float4: each lane is rounded
-// exactly as the scalar operation of the same name, so packed and scalar paths agree bit for bit.
-struct P4 {
-    float2 a, b;
-};
-__device__ __forceinline__ P4 p4(const float4& v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
-__device__ __forceinline__ P4 p4(float v0, float v1, float v2, float v3) {
-    return {make_float2(v0, v1), make_float2(v2, v3)};
-}
-__device__ __forceinline__ float4 f4(const P4& p) { return make_float4(p.a.x, p.a.y, p.b.x, p.b.y); }
-__device__ __forceinline__ float2 sub2(float2 x, float2 y) {  // x - y, one rounding
-    return __ffma2_rn(y, make_float2(-1.f, -1.f), x);
-}
-__device__ __forceinline__ P4 p4add(const P4& x, const P4& y) { return {__fadd2_rn(x.a, y.a), __fadd2_rn(x.b, y.b)}; }
-__device__ __forceinline__ P4 p4sub(const P4& x, const P4& y) { return {sub2(x.a, y.a), sub2(x.b, y.b)}; }
-__device__ __forceinline__ P4 p4mul(const P4& x, const P4& y) { return {__fmul2_rn(x.a, y.a), __fmul2_rn(x.b, y.b)}; }
-__device__ __forceinline__ P4 p4fma(const P4& x, const P4& y, const P4& z) {
-    return {__ffma2_rn(x.a, y.a, z.a), __ffma2_rn(x.b, y.b, z.b)};
-}
-__device__ __forceinline__ P4 p4neg(const P4& x) {
-    return {make_float2(-x.a.x, -x.a.y), make_float2(-x.b.x, -x.b.y)};
-}
-// leapfrog() of an interior cell (G = a- = 1): (2c - prev) + rhs; the factor G = 1 is exact.
-__device__ __forceinline__ P4 p4leap1(const P4& c, const P4& prev, const P4& rhs) {
-    return p4add(p4sub(p4add(c, c), prev), rhs);
-}
-
 // Laplacian of R rows x 4 cells whose first cell sits at halo coordinates (row, col).
 // Both axes in first-difference form: with d_i = v_{i+1} - v_i,
 //   sum_k w_k (v_{c+k} + v_{c-k} - 2 v_c) = sum_{m=0..3} C_m (d_{c+m} - d_{c-m-1}),

@@ -69,6 +69,117 @@ __device__ __forceinline__ void prefetch_pw3(const ModelStep3D& M, const float* 
     }
 }
 
+// Update of one z plane of a thread's 4 cells, once every plane the taps need is in the ring:
+// slot_c holds the current plane (halo tile), slot_c -+ k the planes k below / above; cur_pw
+// the cells' pointwise operands; sinj the injection tile (adjoint, when inj).
+template <int MODE, bool KAHAN>
+__device__ __forceinline__ void cells3(const ModelStep3D& M, const float* smem, int slot_c, int lx, int ly, int x,
+                                       int y, int z, long long off, int shot, int b, long long F, float* outv,
+                                       const Pw3& cur_pw, bool interior_col, int sz, int sy, int sx, float fsrc,
+                                       bool inj, const float* sinj) {
+    const float* cur = smem + slot_c * kPlane3;
+    const float* rp = cur + (ly + 4) * kHX3 + lx + 4;
+    const float4 a = ld4(rp - 4), c = ld4(rp), d = ld4(rp + 4);
+    // x taps in first-difference form (11 shared differences for the 4 cells)
+    const float v[12] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
+    float dx[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) dx[i] = v[i + 1] - v[i];
+    float L[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float acc = M.cxm[0] * (dx[4 + j] - dx[3 + j]);
+#pragma unroll
+        for (int m = 1; m < 4; ++m) acc = fmaf(M.cxm[m], dx[4 + j + m] - dx[3 + j - m], acc);
+        L[j] = acc;
+    }
+    // y and z taps, (v_{+k} - c) + (v_{-k} - c) per pair, in packed FP32x2 (same roundings per lane)
+    P4 acc = p4(L[0], L[1], L[2], L[3]);
+    const P4 cc = p4(c);
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        const P4 up = p4(ld4(rp - k * kHX3)), dn = p4(ld4(rp + k * kHX3));
+        const float w = M.ly[k - 1];
+        acc = p4fma(p4(w, w, w, w), p4add(p4sub(up, cc), p4sub(dn, cc)), acc);
+    }
+    const int cofs = (ly + 4) * kHX3 + lx + 4;
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        int su = slot_c - k, sd = slot_c + k;
+        su += (su < 0) ? kRing : 0;
+        sd -= (sd >= kRing) ? kRing : 0;
+        const P4 up = p4(ld4(smem + su * kPlane3 + cofs));
+        const P4 dn = p4(ld4(smem + sd * kPlane3 + cofs));
+        const float w = M.lz[k - 1];
+        acc = p4fma(p4(w, w, w, w), p4add(p4sub(up, cc), p4sub(dn, cc)), acc);
+    }
+    {
+        const float4 a4 = f4(acc);
+        L[0] = a4.x;
+        L[1] = a4.y;
+        L[2] = a4.z;
+        L[3] = a4.w;
+    }
+    const float4 sv = cur_pw.s;
+    const float4 ov = cur_pw.prev;
+    float src[4] = {0.f, 0.f, 0.f, 0.f};
+    float Dv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) {
+        if (z == sz && y == sy) add_lane(src, sx - x, fsrc);
+    } else if (MODE == STEP3_BORN) {
+        const float4 dd = cur_pw.d;
+        const float4 dmv = cur_pw.dm;
+        L[0] = __fmaf_rn(-dmv.x, dd.x, L[0]);  // Born source -dm Dtt u folded into L
+        L[1] = __fmaf_rn(-dmv.y, dd.y, L[1]);
+        L[2] = __fmaf_rn(-dmv.z, dd.z, L[2]);
+        L[3] = __fmaf_rn(-dmv.w, dd.w, L[3]);
+    } else {
+        const float4 dd = cur_pw.d;
+        Dv[0] = dd.x;
+        Dv[1] = dd.y;
+        Dv[2] = dd.z;
+        Dv[3] = dd.w;
+        if (inj) {
+            const float4 iv = ld4(sinj + ly * kTX + lx);
+            src[0] = iv.x;
+            src[1] = iv.y;
+            src[2] = iv.z;
+            src[3] = iv.w;
+        }
+    }
+    const bool interior = interior_col && (z >= M.pad) && (z < M.pad + M.nz);
+    float o[4], Dw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float G = 1.f, am = 1.f;
+        if (!interior) sponge_pair(sponge_e3(M, z, y, x + j), G, am);
+        const float Fo = __fmul_rn(get(sv, j), __fadd_rn(L[j], src[j]));
+        Dw[j] = __fmul_rn(Fo, M.inv_dt2);
+        o[j] = (x + j < M.Nx) ? leapfrog(G, v[4 + j], am, get(ov, j), Fo) : 0.f;
+    }
+    st4(outv + off, make_float4(o[0], o[1], o[2], o[3]));
+    if ((MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) && M.Dout)
+        st4(M.Dout + (long long)shot * M.Dout_shot_stride + off, make_float4(Dw[0], Dw[1], Dw[2], Dw[3]));
+    if (MODE == STEP3_ADJ) {
+        float* ip = M.img + (long long)(shot * M.nfield + b) * F + off;
+        float4 iv = cur_pw.img;
+        const float t0 = __fmul_rn(-Dv[0], o[0]), t1 = __fmul_rn(-Dv[1], o[1]);
+        const float t2 = __fmul_rn(-Dv[2], o[2]), t3 = __fmul_rn(-Dv[3], o[3]);
+        if (KAHAN) {
+            float* cp = M.comp + (long long)(shot * M.nfield + b) * F + off;
+            float4 cv = cur_pw.cmp;
+            kahan4(iv, cv, t0, t1, t2, t3);
+            st4(cp, cv);
+        } else {
+            iv.x = __fadd_rn(iv.x, t0);
+            iv.y = __fadd_rn(iv.y, t1);
+            iv.z = __fadd_rn(iv.z, t2);
+            iv.w = __fadd_rn(iv.w, t3);
+        }
+        st4(ip, iv);
+    }
+    }
+
 template <int MODE, bool KAHAN>
 __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ StepParams3D p) {
     extern __shared__ __align__(128) float smem[];
@@ -77,16 +188,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ 
     const ModelStep3D& M = p.m;
     const int tid = threadIdx.x;
     const int lx = (tid & 15) << 2, ly = tid >> 4;
-    int t = blockIdx.x;
+    // grid.x = (column tile, chunk) x field with the field fastest: the fields of one tile run as
+    // neighbouring CTAs, so the operands they share (s, a shot's Dtt) come from L2 after the first
+    const int b = (int)(blockIdx.x % M.nfield);
+    int t = (int)(blockIdx.x / M.nfield);
     const int txi = t % M.tiles_x;
     t /= M.tiles_x;
     const int tyi = t % M.tiles_y;
     const int zc = t / M.tiles_y;
     const int x0 = txi * kTX, y0 = tyi * kTY3, z0 = zc * M.ZC;
     const int zend = min(z0 + M.ZC, M.Nz);
-    const int fidx = blockIdx.y;  // shot * nfield + field
-    const int shot = fidx / M.nfield;
-    const int b = fidx - shot * M.nfield;
+    const int shot = blockIdx.y;
     const int n = p.n;
     const int pc = (MODE == STEP3_ADJ) ? ((n + 1) & 1) : (n & 1);
     const int po = pc ^ 1;
@@ -174,105 +286,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ 
             }
             __syncthreads();
         }
-        if (col_ok && z < M.Nz) {
-            const long long off = off0 + (long long)iz * plane_stride;
-            const float* rp = cur + (ly + 4) * kHX3 + lx + 4;
-            const float4 a = ld4(rp - 4), c = ld4(rp), d = ld4(rp + 4);
-            // x taps in first-difference form (11 shared differences for the 4 cells)
-            const float v[12] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
-            float dx[11];
-#pragma unroll
-            for (int i = 0; i < 11; ++i) dx[i] = v[i + 1] - v[i];
-            float L[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float acc = M.cxm[0] * (dx[4 + j] - dx[3 + j]);
-#pragma unroll
-                for (int m = 1; m < 4; ++m) acc = fmaf(M.cxm[m], dx[4 + j + m] - dx[3 + j - m], acc);
-                L[j] = acc;
-            }
-#pragma unroll
-            for (int k = 1; k <= 4; ++k) {
-                const float4 up = ld4(rp - k * kHX3), dn = ld4(rp + k * kHX3);
-                const float w = M.ly[k - 1];
-                L[0] = fmaf(w, (up.x - c.x) + (dn.x - c.x), L[0]);
-                L[1] = fmaf(w, (up.y - c.y) + (dn.y - c.y), L[1]);
-                L[2] = fmaf(w, (up.z - c.z) + (dn.z - c.z), L[2]);
-                L[3] = fmaf(w, (up.w - c.w) + (dn.w - c.w), L[3]);
-            }
-            const int cofs = (ly + 4) * kHX3 + lx + 4;
-#pragma unroll
-            for (int k = 1; k <= 4; ++k) {
-                int su = slot_c - k, sd = slot_c + k;
-                su += (su < 0) ? kRing : 0;
-                sd -= (sd >= kRing) ? kRing : 0;
-                const float4 up = ld4(smem + su * kPlane3 + cofs);
-                const float4 dn = ld4(smem + sd * kPlane3 + cofs);
-                const float w = M.lz[k - 1];
-                L[0] = fmaf(w, (up.x - c.x) + (dn.x - c.x), L[0]);
-                L[1] = fmaf(w, (up.y - c.y) + (dn.y - c.y), L[1]);
-                L[2] = fmaf(w, (up.z - c.z) + (dn.z - c.z), L[2]);
-                L[3] = fmaf(w, (up.w - c.w) + (dn.w - c.w), L[3]);
-            }
-            const float4 sv = cur_pw.s;
-            const float4 ov = cur_pw.prev;
-            float src[4] = {0.f, 0.f, 0.f, 0.f};
-            float Dv[4] = {0.f, 0.f, 0.f, 0.f};
-            if (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) {
-                if (z == sz && y == sy) add_lane(src, sx - x, fsrc);
-            } else if (MODE == STEP3_BORN) {
-                const float4 dd = cur_pw.d;
-                const float4 dmv = cur_pw.dm;
-                L[0] = __fmaf_rn(-dmv.x, dd.x, L[0]);  // Born source -dm Dtt u folded into L
-                L[1] = __fmaf_rn(-dmv.y, dd.y, L[1]);
-                L[2] = __fmaf_rn(-dmv.z, dd.z, L[2]);
-                L[3] = __fmaf_rn(-dmv.w, dd.w, L[3]);
-            } else {
-                const float4 dd = cur_pw.d;
-                Dv[0] = dd.x;
-                Dv[1] = dd.y;
-                Dv[2] = dd.z;
-                Dv[3] = dd.w;
-                if (inj) {
-                    const float4 iv = ld4(sinj + ly * kTX + lx);
-                    src[0] = iv.x;
-                    src[1] = iv.y;
-                    src[2] = iv.z;
-                    src[3] = iv.w;
-                }
-            }
-            const bool interior = interior_col && (z >= M.pad) && (z < M.pad + M.nz);
-            float o[4], Dw[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float G = 1.f, am = 1.f;
-                if (!interior) sponge_pair(sponge_e3(M, z, y, x + j), G, am);
-                const float Fo = __fmul_rn(get(sv, j), __fadd_rn(L[j], src[j]));
-                Dw[j] = __fmul_rn(Fo, M.inv_dt2);
-                o[j] = (x + j < M.Nx) ? leapfrog(G, v[4 + j], am, get(ov, j), Fo) : 0.f;
-            }
-            st4(outv + off, make_float4(o[0], o[1], o[2], o[3]));
-            if ((MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) && M.Dout)
-                st4(M.Dout + (long long)shot * M.Dout_shot_stride + off, make_float4(Dw[0], Dw[1], Dw[2], Dw[3]));
-            if (MODE == STEP3_ADJ) {
-                float* ip = M.img + (long long)(shot * M.nfield + b) * F + off;
-                float4 iv = cur_pw.img;
-                const float t0 = __fmul_rn(-Dv[0], o[0]), t1 = __fmul_rn(-Dv[1], o[1]);
-                const float t2 = __fmul_rn(-Dv[2], o[2]), t3 = __fmul_rn(-Dv[3], o[3]);
-                if (KAHAN) {
-                    float* cp = M.comp + (long long)(shot * M.nfield + b) * F + off;
-                    float4 cv = cur_pw.cmp;
-                    kahan4(iv, cv, t0, t1, t2, t3);
-                    st4(cp, cv);
-                } else {
-                    iv.x = __fadd_rn(iv.x, t0);
-                    iv.y = __fadd_rn(iv.y, t1);
-                    iv.z = __fadd_rn(iv.z, t2);
-                    iv.w = __fadd_rn(iv.w, t3);
-                }
-                st4(ip, iv);
-            }
-        }
+        if (col_ok && z < M.Nz)
+            cells3<MODE, KAHAN>(M, smem, slot_c, lx, ly, x, y, z, off0 + (long long)iz * plane_stride, shot, b, F, outv,
+                                cur_pw, interior_col, sz, sy, sx, fsrc, inj, sinj);
         __syncthreads();  // the slot of plane k = iz is free again
         if (tid == 0) {
             const int k = iz + kRing;
@@ -300,6 +316,146 @@ __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ 
     }
 }
 
+constexpr int kWs3Threads = kThreads + 32;  // eight consumer warps + one producer warp
+
+// Pipelined variant for the forward modes (incident, nonlinear sampling, Born): one producer warp
+// streams the halo'd planes into the ring (per-slot full / empty mbarriers, one arrival per
+// consumer warp on release), so the consumer warps never meet at a CTA-wide barrier inside the
+// plane loop; each releases the oldest plane of its window as soon as it is done with it.  The
+// per-cell arithmetic is cells3, identical to k_step3d.  Every wait is bounded.
+template <int MODE>
+__global__ void __launch_bounds__(kWs3Threads, MODE == STEP3_BORN ? 2 : 3) k_step3d_ws(const __grid_constant__ StepParams3D p) {
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t full[kRing], empty[kRing];
+    __shared__ int srec[kZC3D + 1];  // receiver CSR bounds of this column tile's planes
+    constexpr bool SAMPLE = (MODE == STEP3_BORN || MODE == STEP3_INC_SAMPLE);
+    const ModelStep3D& M = p.m;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // grid.x = (column tile, chunk) x field with the field fastest: the fields of one tile run as
+    // neighbouring CTAs, so the operands they share (s, a shot's Dtt) come from L2 after the first
+    const int b = (int)(blockIdx.x % M.nfield);
+    int t = (int)(blockIdx.x / M.nfield);
+    const int txi = t % M.tiles_x;
+    t /= M.tiles_x;
+    const int tyi = t % M.tiles_y;
+    const int zc = t / M.tiles_y;
+    const int x0 = txi * kTX, y0 = tyi * kTY3, z0 = zc * M.ZC;
+    const int zend = min(z0 + M.ZC, M.Nz);
+    const int shot = blockIdx.y;
+    const int n = p.n;
+    const int pc = n & 1, po = pc ^ 1;
+    const long long F = M.F;
+    const int vol_cur = shot * M.nvol_shot + 2 * b + pc;
+    float* outv = M.state + (long long)(shot * M.nvol_shot + 2 * b + po) * F;
+    const int nloc = zend - z0;
+    const int nplanes = nloc + 8;
+
+    if (tid == 0) {
+        for (int i = 0; i < kRing; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kThreads / 32);
+        }
+        fence_mbar_init();
+    }
+    if (SAMPLE && tid <= nloc) srec[tid] = M.rec_ptr[(tyi * M.tiles_x + txi) * M.Nz + z0 + tid];
+    __syncthreads();
+
+    if (warp == kThreads / 32) {  // ---------------- producer warp
+        if (lane != 0) return;
+        int sl = 0;
+        uint32_t eph = 0;  // phase of empty[sl] to wait for, once the ring has wrapped
+        for (int k = 0; k < nplanes; ++k) {
+            if (k >= kRing && !mbar_wait_bounded(&empty[sl], eph)) {
+                set_dev_error(p.err, DEVERR_TIMEOUT);
+                return;
+            }
+            mbar_expect_tx(&full[sl], kPlaneBytes3);
+            tma_load_4d(smem + sl * kPlane3, &M.tm, x0 - 4, y0 - 4, z0 - 4 + k, vol_cur, &full[sl]);
+            if (++sl == kRing) {
+                sl = 0;
+                if (k + 1 >= 2 * kRing) eph ^= 1u;  // the wait for plane k + 1 is for its (k+1)/kRing - 1 th release
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumer warps
+    const int lx = (tid & 15) << 2, ly = tid >> 4;
+    const int x = x0 + lx, y = y0 + ly;
+    const bool col_ok = (x < M.Nx) && (y < M.Ny);
+    const bool interior_col = (x >= M.pad) && (x + 3 < M.pad + M.nx) && (y >= M.pad) && (y < M.pad + M.ny);
+    const int sz = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.src[3 * shot] : -1;
+    const int sy = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.src[3 * shot + 1] : -1;
+    const int sx = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.src[3 * shot + 2] : -1;
+    const float fsrc = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.wavelet[n] * M.vol_inv : 0.f;
+    const long long plane_stride = (long long)M.Ny * M.P;
+    const long long off0 = ((long long)z0 * M.Ny + y) * M.P + x;
+    int slot_c = 4, slot_w = 8;  // slots of the current plane (k = iz + 4) and of k = iz + 8
+    uint32_t ph_w = 0;
+
+    auto plane = [&](int iz, const Pw3& cur_pw, Pw3& nxt_pw) -> bool {
+        const int z = z0 + iz;
+        if (col_ok && iz + 1 < nloc)
+            load_pw3<MODE, false>(M, outv, off0 + (long long)(iz + 1) * plane_stride, shot, b, F, nxt_pw);
+        if (col_ok && iz + kPrefetch3 < nloc)
+            prefetch_pw3<MODE, false>(M, outv, off0 + (long long)(iz + kPrefetch3) * plane_stride, shot, b, F);
+        const int kfirst = (iz == 0) ? 0 : iz + 8;
+        for (int k = kfirst; k <= iz + 8; ++k) {
+            const bool ok = (iz == 0) ? mbar_wait_bounded(&full[k], 0u) : mbar_wait_bounded(&full[slot_w], ph_w);
+            if (!ok) {
+                set_dev_error(p.err, DEVERR_TIMEOUT);
+                return false;
+            }
+        }
+        if (SAMPLE) {  // receivers of this plane, from its staged tile
+            const int rbeg = srec[iz], rend = srec[iz + 1];
+            if (rend > rbeg) {
+                const float* cur = smem + slot_c * kPlane3;
+                float* dout = M.data + (long long)shot * M.dss + (long long)b * M.dts + (long long)n * M.nr;
+                for (int i = rbeg + tid; i < rend; i += kThreads) {
+                    const int r = M.rec_idx[i];
+                    dout[r] = cur[(M.rec_zyx[3 * r + 1] - y0 + 4) * kHX3 + (M.rec_zyx[3 * r + 2] - x0 + 4)];
+                }
+            }
+        }
+        if (col_ok && z < M.Nz)
+            cells3<MODE, false>(M, smem, slot_c, lx, ly, x, y, z, off0 + (long long)iz * plane_stride, shot, b, F,
+                                outv, cur_pw, interior_col, sz, sy, sx, fsrc, false, nullptr);
+        __syncwarp();
+        if (lane == 0) {  // this warp is done with plane k = iz (the bottom of its window)
+            int sf = slot_c - 4;
+            sf += (sf < 0) ? kRing : 0;
+            mbar_arrive(&empty[sf]);
+        }
+        slot_c = (slot_c + 1 == kRing) ? 0 : slot_c + 1;
+        if (++slot_w == kRing) {
+            slot_w = 0;
+            ph_w ^= 1u;
+        }
+        return true;
+    };
+
+    Pw3 pa, pb;
+    if (col_ok && nloc > 0) load_pw3<MODE, false>(M, outv, off0, shot, b, F, pa);
+    for (int iz = 0; iz < nloc; iz += 2) {
+        if (!plane(iz, pa, pb)) return;
+        if (iz + 1 < nloc && !plane(iz + 1, pb, pa)) return;
+    }
+}
+
+template <int MODE>
+static cudaError_t launch3_ws(const StepParams3D& p, dim3 grid, cudaStream_t st) {
+    const size_t sm = (size_t)kRing * kPlaneBytes3;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_step3d_ws<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_step3d_ws<MODE><<<grid, kWs3Threads, sm, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <int MODE, bool KAHAN>
 static cudaError_t launch3(const StepParams3D& p, dim3 grid, cudaStream_t st) {
     const size_t sm = step3d_smem_bytes();
@@ -313,10 +469,18 @@ static cudaError_t launch3(const StepParams3D& p, dim3 grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_step3d(int mode, bool kahan, const StepParams3D& p, cudaStream_t st) {
+cudaError_t launch_step3d(int mode, bool kahan, bool pipelined, const StepParams3D& p, cudaStream_t st) {
     const ModelStep3D& M = p.m;
-    dim3 grid(M.tiles_x * M.tiles_y * M.zchunks, M.nshots * M.nfield);
+    dim3 grid(M.tiles_x * M.tiles_y * M.zchunks * M.nfield, M.nshots);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+    if (pipelined) {
+        switch (mode) {
+            case STEP3_INC: return launch3_ws<STEP3_INC>(p, grid, st);
+            case STEP3_INC_SAMPLE: return launch3_ws<STEP3_INC_SAMPLE>(p, grid, st);
+            case STEP3_BORN: return launch3_ws<STEP3_BORN>(p, grid, st);
+            default: break;  // the adjoint keeps the one-barrier-per-plane kernel
+        }
+    }
     switch (mode) {
         case STEP3_INC: return launch3<STEP3_INC, false>(p, grid, st);
         case STEP3_INC_SAMPLE: return launch3<STEP3_INC_SAMPLE, false>(p, grid, st);

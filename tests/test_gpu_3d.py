@@ -58,6 +58,22 @@ def test_born_data_3d(cuda_device, small3d):
             assert rel(d[b, s], born[b, s]) < 2e-5, (b, s)
 
 
+def test_forward_kernels_3d_agree(cuda_device, small3d):
+    """The producer-warp pipelined 3D forward kernels and the one-barrier-per-plane kernels run the
+    same per-cell arithmetic: F and H agree bit for bit."""
+    wl, prob, born, hes = small3d
+    y = dev(wl.trials)
+    out = []
+    for pipe in (0, 2):
+        p = make_probe(wl)
+        p.set_option("pipeline", pipe)
+        out.append((p.apply_F(y), p.apply_H(y)))
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+    for b in range(2):
+        assert rel(out[1][1][b].cpu().numpy(), hes[b]) < 1e-4
+
+
 @pytest.mark.parametrize("snap,tol,wave", [("fp32", 1e-4, 0), ("fp32", 1e-4, 3), ("fp16", 2e-3, 0)])
 def test_hessian_3d(cuda_device, small3d, snap, tol, wave):
     wl, prob, born, hes = small3d
