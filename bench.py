@@ -213,8 +213,11 @@ def kernel_source_hash(name):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def kernel_label(pipeline, adjoint):
-    """Kernel name and source file of the 2D forward / adjoint step variant the handle ran."""
+def kernel_label(pipeline, adjoint, ndim=2):
+    """Kernel name and source file of the forward / adjoint step variant the handle ran."""
+    if ndim == 3:
+        return (("k_step3d<ADJ, kahan>" if adjoint else
+                 "k_step3d_ws<BORN> / <INC> (3D forward steps, one field kind per launch)"), "stencil3d.cu")
     if pipeline:
         name = (f"k_adj2d_ws<nbc, kahan, S={pipeline}>" if adjoint else
                 f"k_fwd2d_ws<FWD_BORN, S={pipeline}> (fused incident + Born step, warp-specialised TMA ring)")
@@ -254,6 +257,99 @@ def weak_scaling_value(units_per_rank, world, ms_step_max):
     """Whole-job throughput: units processed by all ranks / the slowest rank's step time."""
     return units_per_rank * world / (ms_step_max * 1e-3)
 
+
+
+# ---------------------------------------------------------------------------
+# Configurations 3 (three models in one group) and 4 (gradient of the misfit)
+# ---------------------------------------------------------------------------
+def run_group_or_gradient(a, cpu):
+    """One JSON line for config 3 (probe_apply_H_group over the three layered models, p = 8 trials
+    each, FP16 checkpoints) or config 4 (one misfit gradient: nonlinear forward at m_true, then
+    probe_gradient of the residual against the data at m0, FP16 checkpoints); single GPU."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ge._build_module().build()
+    from paper_1101_3615_gb300 import Probe, apply_H_group
+    from workloads import CONFIG_NAMES, make_config
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+
+    def probe_of(w, snap="fp16"):
+        p = Probe(w.m0, w.h, w.dt, w.nt, w.pad, w.src, w.rec, w.wavelet, snapshot_dtype=snap)
+        p.set_option("check_finite", 0)
+        p.set_option("use_graph", 1)
+        return p
+
+    if a.config == 3:
+        wls = [make_config(3, m) for m in range(3)]
+        probes = [probe_of(w) for w in wls]
+        dms = [torch.tensor(w.trials, device=dev) for w in wls]
+        outs = [torch.empty_like(d) for d in dms]
+        step = lambda: apply_H_group(probes, dms, outs)
+        units = sum(w.trials.shape[0] for w in wls)
+        cells = sum((2 + 2 * w.trials.shape[0]) * float(w.cells_padded()) * (w.nt - 1) * w.ns for w in wls)
+        unit_key, shape = "h_applies_per_s", [list(w.padded_shape) for w in wls]
+        h0 = probes[0]
+    else:
+        w = make_config(4)
+        wls = [w]
+        h0 = probe_of(w)
+        m_true = torch.tensor(w.extra["m_true"], device=dev)
+        m0 = torch.tensor(w.m0, device=dev)
+        d_obs = h0.forward_nonlinear(m_true)
+        d_cur = torch.empty_like(d_obs)
+        g = torch.empty_like(m0)
+
+        def step():
+            h0.forward_nonlinear(m0, out=d_cur)
+            h0.gradient(m0, d_cur - d_obs, out=g)
+        units = 1
+        cells = 3.0 * float(w.cells_padded()) * (w.nt - 1) * w.ns  # nonlinear forward, recompute, adjoint
+        unit_key, shape = "gradients_per_s", list(w.padded_shape)
+
+    h0.set_option("timing", 2)
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms_step = e0.elapsed_time(e1) / a.steps
+    st = h0.stats()
+    h0.set_option("timing", 0)
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if st["ms_forward"] > 0 and st["launches_forward"] > 0:
+        bpl, mpl = st["bytes_forward"] / st["launches_forward"], st["ms_forward"] / st["launches_forward"]
+        ach = bpl / (mpl * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "kernel": "forward step of the last timed step (k_fwd2d_ws / k_fwd2d)", "bytes_per_launch": bpl,
+                "avg_launch_ms": mpl, "peak_kind": f"{peak_kind} hbm_gbs (copy)"}
+    line = {
+        "metric": METRIC, "value": cells / (ms_step * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": CONFIG_NAMES[a.config], "grid_padded": shape, "snapshots": "fp16",
+                   "shots": [x.ns for x in wls], "trials": [x.trials.shape[0] for x in wls] if a.config == 3 else 0,
+                   "nt": wls[0].nt, "cuda_graph": True, "autotuned": True},
+        unit_key: units / (ms_step * 1e-3),
+        "roofline": roof,
+        "gpu_launches": int(st["launches_total"]) * a.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
 
 # ---------------------------------------------------------------------------
 def main():
@@ -308,11 +404,17 @@ def main():
     # CPU baseline first (spawned pool, before any CUDA work), rank 0 at N=1 only
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
-        nsh, nts = min(16, wl.ns, os.cpu_count() or 1), 251
+        nts = {4: 101, 5: 3}.get(a.config, 251)  # about 10-30 s of oracle work
+        nsh = min(16, wl.ns, os.cpu_count() or 1)
         v, cores, wall = oracle_sample(a.config, nsh, nts)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{nsh} shots x {nts - 1} steps of H (F then F*) on the full "
-                         f"{wl.padded_shape[0]}x{wl.padded_shape[1]} padded grid, {wall:.1f} s wall"}
+                         f"{'x'.join(str(n) for n in wl.padded_shape)} padded grid"
+                         f"{' of the first model' if a.config == 3 else ''}, {wall:.1f} s wall"}
+    if a.config in (3, 4):
+        if rank == 0:
+            run_group_or_gradient(a, cpu)
+        return
 
     import numpy as np
     import torch
@@ -342,7 +444,8 @@ def main():
 
     p = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet, snapshot_dtype=a.snapshot)
     p.set_option("check_finite", 0)
-    p.set_option("tile_z", 16)
+    if len(wl.shape) == 2:
+        p.set_option("tile_z", 16)
     p.set_option("use_graph", 1)      # each shot wave's sweeps replayed as one CUDA graph
     if a.fixed:
         pf, pa, rows, grp = (int(v) for v in a.fixed.split(","))
@@ -412,20 +515,24 @@ def main():
     e2e = {"value": cells_per_h * world / e2e_s / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": int(dm_host.nbytes), "d2h_bytes_per_step": int(out_host.nbytes)}
 
-    # FP32 dot-product test on the full workload (stated error): FP32 checkpoints, with which
-    # F* is the transpose of F to round-off (16-bit checkpoints perturb Dtt u^n)
+    # FP32 dot-product test on the full workload (stated error), first trial: FP32 checkpoints,
+    # with which F* is the transpose of F to round-off (16-bit checkpoints perturb Dtt u^n).
+    # The timed handle's workspace is released first (3D workspaces are large).
+    del p
+    torch.cuda.synchronize(dev)
     p32 = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet, snapshot_dtype="fp32")
     p32.set_option("check_finite", 0)
-    d = p32.apply_F(dm)
+    dm1 = dm[:1].contiguous()
+    d = p32.apply_F(dm1)
     img = p32.apply_Fadj(d)
-    lhs = float(torch.sum(d.double() ** 2))
-    rhs = float(torch.sum(dm.double() * img.double()))
+    lhs = float(torch.sum(d * d, dtype=torch.float64))
+    rhs = float(torch.sum(dm1 * img, dtype=torch.float64))
     dot_err = abs(lhs - rhs) / abs(lhs)
-    del d, img, p32
+    del d, img, p32, dm1
 
     # same step with Dtt u^n of every time step kept in HBM (no checkpoint recompute)
     hist = None
-    if not a.no_history:
+    if not a.no_history and len(wl.shape) == 2:  # (the Dtt history is a 2D option)
         ph = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src, wl.rec, wl.wavelet)
         for k, v in (("check_finite", 0), ("tile_z", 16), ("use_graph", 1), ("dtt_history", 1)):
             ph.set_option(k, v)
@@ -454,31 +561,36 @@ def main():
             hist = {"unavailable": str(ex).splitlines()[0][:200]}
         del ph
 
-    # plain per-shot FP32 path: one shot resident at a time, no shot grouping
+    # plain per-(shot, trial) FP32 path: one shot resident at a time, one trial per call, no shot
+    # grouping (so the incident field is recomputed for every trial)
     plain = None
     if not a.no_plain:
         nsub = min(4, wl.ns)
         pp = Probe(wl.m0, wl.h, wl.dt, wl.nt, wl.pad, wl.src[:nsub], wl.rec, wl.wavelet)
         for k, v in (("check_finite", 0), ("shot_wave", 1), ("shot_group", 1), ("tile_z", 16)):
             pp.set_option(k, v)
-        pp.apply_H(dm, out=out)
+        y1 = dm[:1].contiguous()
+        o1 = torch.empty_like(y1)
+        pp.apply_H(y1, out=o1)
         torch.cuda.synchronize(dev)
         ep0 = torch.cuda.Event(enable_timing=True)
         ep1 = torch.cuda.Event(enable_timing=True)
         ep0.record(stream)
-        pp.apply_H(dm, out=out)
+        pp.apply_H(y1, out=o1)
         ep1.record(stream)
         torch.cuda.synchronize(dev)
-        per_shot_ms = ep0.elapsed_time(ep1) / nsub
-        plain_ms = per_shot_ms * wl.ns
+        per_shot_trial_ms = ep0.elapsed_time(ep1) / nsub
+        plain_ms = per_shot_trial_ms * wl.ns * ntr  # every (shot, trial) of one H application
         plain = {"value": cells_plain / (plain_ms * 1e-3) / 1e9, "unit": UNIT,
-                 "h_applies_per_s": wl.trials.shape[0] / (plain_ms * 1e-3),
+                 "h_applies_per_s": ntr / (plain_ms * 1e-3),
                  "ms_per_h": plain_ms,
-                 "how": f"one shot resident at a time, timed on {nsub} shots and scaled to {wl.ns}"}
-        del pp
+                 "how": f"one shot resident at a time and one trial per call, timed on {nsub} shots x 1 "
+                        f"trial and scaled to {wl.ns} shots x {ntr} trials"}
+        del pp, y1, o1
 
-    fwd_name, fwd_src = kernel_label(stats["pipeline_forward"], False)
-    adj_name, adj_src = kernel_label(stats["pipeline_adjoint"], True)
+    live_mb = wl.ns * (2 + 2 * ntr) * wl.cells_padded() * 4 / 1e6
+    fwd_name, fwd_src = kernel_label(stats["pipeline_forward"], False, len(wl.shape))
+    adj_name, adj_src = kernel_label(stats["pipeline_adjoint"], True, len(wl.shape))
     traffic = ncu_traffic("fwd_born", fwd_src, {"pipeline_forward": stats["pipeline_forward"],
                                                 "pipeline_rows": stats["pipeline_rows"]})
     line = {
@@ -493,10 +605,11 @@ def main():
                    "tile_z": stats["tile_z"], "pipeline_forward": stats["pipeline_forward"],
                    "pipeline_adjoint": stats["pipeline_adjoint"], "cuda_graph": True,
                    "autotuned": not a.fixed,
-                   "l2": f"inputs larger than L2: {wl.ns} shots x 4 field planes x "
-                         f"{wl.cells_padded() * 4 / 1e6:.2f} MB = "
-                         f"{wl.ns * 4 * wl.cells_padded() * 4 / 1e6:.0f} MB live state per step "
-                         f"> {L2_BYTES / 1e6:.0f} MB L2; no flush",
+                   "l2": (f"inputs larger than L2: {wl.ns} shots x {2 + 2 * ntr} field planes x "
+                          f"{wl.cells_padded() * 4 / 1e6:.2f} MB = {live_mb:.0f} MB live state per step "
+                          f"> {L2_BYTES / 1e6:.0f} MB L2; no flush") if live_mb * 1e6 > L2_BYTES else
+                         (f"working set {live_mb:.1f} MB fits the {L2_BYTES / 1e6:.0f} MB L2 (a small-grid "
+                          f"case: each state plane is revisited every time step); no flush"),
                    "parallelism": f"shots x{world} ranks (independent jobs)"},
         "h_applies_per_s": h_per_s,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

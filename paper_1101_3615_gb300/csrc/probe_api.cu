@@ -1869,6 +1869,11 @@ extern "C" probe_status probe_apply_H_group(const probe_t* models, int nmodels, 
         h0->stats.cell_updates_forward += cells * steps * h->ns * (1 + nb[k]);
         h0->stats.cell_updates_recompute += cells * steps * h->ns;
         h0->stats.cell_updates_adjoint += cells * steps * h->ns * nb[k];
+        // algorithmic bytes, as for probe_apply_H
+        h0->stats.bytes_forward += cells * steps * h->ns * (16.0 + 16.0 * nb[k]);
+        h0->stats.bytes_recompute += cells * steps * h->ns * 20.0;
+        h0->stats.bytes_adjoint += cells * steps * (12.0 * h->ns * nb[k] + 4.0 * h->ns +
+                                                    (double)sw.jobs[k].groups * (4.0 + (h->kahan ? 16.0 : 8.0) * nb[k]));
         TRY(finish_call(h, st, any_host, outs[k], (long long)nb[k] * h->nmodel));
     }
     if (h0->opt_timing) {
