@@ -81,3 +81,29 @@ def test_host_side_validation_rejects_bad_arguments(built_lib):
     g3.ndim = 4
     st, h = _create(built_lib, g3, m0, [[2, 3]], [[0, 0]], w, 50, 1e-3)
     assert st == -1
+
+
+def _header():
+    return open(os.path.join(ROOT, "include", "probe.h")).read()
+
+
+def test_binding_options_match_the_header():
+    """Every PROBE_OPT_* of the header has the same value in the binding's option table."""
+    from paper_1101_3615_gb300.binding import OPT
+    decl = {m.group(1).lower(): int(m.group(2))
+            for m in re.finditer(r"PROBE_OPT_(\w+)\s*=\s*(\d+)", _header())}
+    assert decl, "no options declared"
+    assert sorted(decl.values()) == sorted(OPT.values())
+    for name, val in decl.items():
+        assert OPT.get(name) == val, (name, val, OPT.get(name))
+
+
+def test_binding_stats_struct_matches_the_header():
+    """probe_stats: the binding's ctypes fields have the header's names, order and C types."""
+    from paper_1101_3615_gb300.binding import probe_stats
+    head = _header()
+    end = head.index("} probe_stats;")
+    body = head[head.rindex("typedef struct {", 0, end):end]
+    fields = re.findall(r"^\s*(double|long long|int)\s+(\w+);", body, re.M)
+    ctype = {"double": C.c_double, "long long": C.c_longlong, "int": C.c_int}
+    assert [(n, ctype[t]) for t, n in fields] == [(n, t) for n, t in probe_stats._fields_]
