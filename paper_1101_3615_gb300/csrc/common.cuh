@@ -68,8 +68,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
-// 3D tiled TMA load of one box into shared memory, completing on `bar`.
-// The innermost coordinate x must be a multiple of 4 (16 bytes of FP32).
 // Rounding-explicit pieces of the explicit time update u^{n+1} = G (2 u^n - a- u^{n-1} + rhs)
 // (Sec. 2 scheme with the sponge).  Every product and sum is one IEEE operation written
 // out, so the compiler cannot fuse them differently in different kernel instantiations:
@@ -86,6 +84,8 @@ __device__ __forceinline__ void sponge_pair(float e, float& G, float& am) {
     }
 }
 
+// 3D tiled TMA load of one box into shared memory, completing on `bar`.
+// The innermost coordinate x must be a multiple of 4 (16 bytes of FP32).
 __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* map, int x, int y,
                                             int z, uint64_t* bar) {
     asm volatile(
