@@ -36,6 +36,21 @@ __device__ __forceinline__ float sponge_e3(const ModelStep3D& M, int z, int y, i
     return __fmaf_rn(M.cz, (float)(rz * rz), __fmaf_rn(M.cy, (float)(ry * ry), __fmul_rn(M.cx, (float)(rx * rx))));
 }
 
+// Sponge factors G, a- of a thread's 4 cells on the planes where z is not in the sponge: there
+// the exponent has no z part, so they depend on the column alone and are formed once per CTA
+// (1 on interior columns).  Same roundings as sponge_pair(sponge_e3(...)) on those planes.
+__device__ __forceinline__ void sponge_col3(const ModelStep3D& M, int y, int x, float4& G, float4& A) {
+    float g[4], a[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        g[j] = 1.f;
+        a[j] = 1.f;
+        sponge_pair(sponge_e3(M, M.pad, y, x + j), g[j], a[j]);
+    }
+    G = make_float4(g[0], g[1], g[2], g[3]);
+    A = make_float4(a[0], a[1], a[2], a[3]);
+}
+
 // Pointwise operands of one plane of a thread's 4 cells, loaded one plane ahead of their use
 // so that their HBM latency overlaps the previous plane's work.
 struct Pw3 {
@@ -75,8 +90,8 @@ __device__ __forceinline__ void prefetch_pw3(const ModelStep3D& M, const float* 
 template <int MODE, bool KAHAN>
 __device__ __forceinline__ void cells3(const ModelStep3D& M, const float* smem, int slot_c, int lx, int ly, int x,
                                        int y, int z, long long off, int shot, int b, long long F, float* outv,
-                                       const Pw3& cur_pw, bool interior_col, int sz, int sy, int sx, float fsrc,
-                                       bool inj, const float* sinj) {
+                                       const Pw3& cur_pw, const float4& Gc, const float4& Ac, int sz, int sy,
+                                       int sx, float fsrc, bool inj, const float* sinj) {
     const float* cur = smem + slot_c * kPlane3;
     const float* rp = cur + (ly + 4) * kHX3 + lx + 4;
     const float4 a = ld4(rp - 4), c = ld4(rp), d = ld4(rp + 4);
@@ -147,12 +162,16 @@ __device__ __forceinline__ void cells3(const ModelStep3D& M, const float* smem, 
             src[3] = iv.w;
         }
     }
-    const bool interior = interior_col && (z >= M.pad) && (z < M.pad + M.nz);
+    const bool zin = (z >= M.pad) && (z < M.pad + M.nz);
     float o[4], Dw[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float G = 1.f, am = 1.f;
-        if (!interior) sponge_pair(sponge_e3(M, z, y, x + j), G, am);
+        float G = get(Gc, j), am = get(Ac, j);  // planes outside the z sponge: the column's factors
+        if (!zin) {
+            G = 1.f;
+            am = 1.f;
+            sponge_pair(sponge_e3(M, z, y, x + j), G, am);
+        }
         const float Fo = __fmul_rn(get(sv, j), __fadd_rn(L[j], src[j]));
         Dw[j] = __fmul_rn(Fo, M.inv_dt2);
         o[j] = (x + j < M.Nx) ? leapfrog(G, v[4 + j], am, get(ov, j), Fo) : 0.f;
@@ -223,7 +242,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ 
 
     const int x = x0 + lx, y = y0 + ly;
     const bool col_ok = (x < M.Nx) && (y < M.Ny);
-    const bool interior_col = (x >= M.pad) && (x + 3 < M.pad + M.nx) && (y >= M.pad) && (y < M.pad + M.ny);
+    float4 Gc, Ac;
+    sponge_col3(M, y, x, Gc, Ac);
     const int sz = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.src[3 * shot] : -1;
     const int sy = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.src[3 * shot + 1] : -1;
     const int sx = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.src[3 * shot + 2] : -1;
@@ -288,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ 
         }
         if (col_ok && z < M.Nz)
             cells3<MODE, KAHAN>(M, smem, slot_c, lx, ly, x, y, z, off0 + (long long)iz * plane_stride, shot, b, F, outv,
-                                cur_pw, interior_col, sz, sy, sx, fsrc, inj, sinj);
+                                cur_pw, Gc, Ac, sz, sy, sx, fsrc, inj, sinj);
         __syncthreads();  // the slot of plane k = iz is free again
         if (tid == 0) {
             const int k = iz + kRing;
@@ -324,7 +344,7 @@ constexpr int kWs3Threads = kThreads + 32;  // eight consumer warps + one produc
 // plane loop; each releases the oldest plane of its window as soon as it is done with it.  The
 // per-cell arithmetic is cells3, identical to k_step3d.  Every wait is bounded.
 template <int MODE>
-__global__ void __launch_bounds__(kWs3Threads, MODE == STEP3_BORN ? 2 : 3) k_step3d_ws(const __grid_constant__ StepParams3D p) {
+__global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_constant__ StepParams3D p) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[kRing], empty[kRing];
     __shared__ int srec[kZC3D + 1];  // receiver CSR bounds of this column tile's planes
@@ -383,7 +403,8 @@ __global__ void __launch_bounds__(kWs3Threads, MODE == STEP3_BORN ? 2 : 3) k_ste
     const int lx = (tid & 15) << 2, ly = tid >> 4;
     const int x = x0 + lx, y = y0 + ly;
     const bool col_ok = (x < M.Nx) && (y < M.Ny);
-    const bool interior_col = (x >= M.pad) && (x + 3 < M.pad + M.nx) && (y >= M.pad) && (y < M.pad + M.ny);
+    float4 Gc, Ac;
+    sponge_col3(M, y, x, Gc, Ac);
     const int sz = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.src[3 * shot] : -1;
     const int sy = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.src[3 * shot + 1] : -1;
     const int sx = (MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) ? M.src[3 * shot + 2] : -1;
@@ -393,10 +414,12 @@ __global__ void __launch_bounds__(kWs3Threads, MODE == STEP3_BORN ? 2 : 3) k_ste
     int slot_c = 4, slot_w = 8;  // slots of the current plane (k = iz + 4) and of k = iz + 8
     uint32_t ph_w = 0;
 
-    auto plane = [&](int iz, const Pw3& cur_pw, Pw3& nxt_pw) -> bool {
+    auto plane = [&](int iz) -> bool {
         const int z = z0 + iz;
-        if (col_ok && iz + 1 < nloc)
-            load_pw3<MODE, false>(M, outv, off0 + (long long)(iz + 1) * plane_stride, shot, b, F, nxt_pw);
+        // this plane's pointwise operands (prefetched into L2 earlier): issued before the ring
+        // wait so that their latency overlaps the wait and the stencil
+        Pw3 cur_pw;
+        if (col_ok) load_pw3<MODE, false>(M, outv, off0 + (long long)iz * plane_stride, shot, b, F, cur_pw);
         if (col_ok && iz + kPrefetch3 < nloc)
             prefetch_pw3<MODE, false>(M, outv, off0 + (long long)(iz + kPrefetch3) * plane_stride, shot, b, F);
         const int kfirst = (iz == 0) ? 0 : iz + 8;
@@ -420,7 +443,7 @@ __global__ void __launch_bounds__(kWs3Threads, MODE == STEP3_BORN ? 2 : 3) k_ste
         }
         if (col_ok && z < M.Nz)
             cells3<MODE, false>(M, smem, slot_c, lx, ly, x, y, z, off0 + (long long)iz * plane_stride, shot, b, F,
-                                outv, cur_pw, interior_col, sz, sy, sx, fsrc, false, nullptr);
+                                outv, cur_pw, Gc, Ac, sz, sy, sx, fsrc, false, nullptr);
         __syncwarp();
         if (lane == 0) {  // this warp is done with plane k = iz (the bottom of its window)
             int sf = slot_c - 4;
@@ -435,12 +458,9 @@ __global__ void __launch_bounds__(kWs3Threads, MODE == STEP3_BORN ? 2 : 3) k_ste
         return true;
     };
 
-    Pw3 pa, pb;
-    if (col_ok && nloc > 0) load_pw3<MODE, false>(M, outv, off0, shot, b, F, pa);
-    for (int iz = 0; iz < nloc; iz += 2) {
-        if (!plane(iz, pa, pb)) return;
-        if (iz + 1 < nloc && !plane(iz + 1, pb, pa)) return;
-    }
+#pragma unroll 2
+    for (int iz = 0; iz < nloc; ++iz)
+        if (!plane(iz)) return;
 }
 
 template <int MODE>
