@@ -258,10 +258,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ 
     uint32_t ph_w = 0;
 
     // one z plane; the operands of this plane arrived in cur_pw, the next plane's go to nxt_pw
-    auto plane = [&](int iz, const Pw3& cur_pw, Pw3& nxt_pw) -> bool {
+    auto plane = [&](int iz) -> bool {
         const int z = z0 + iz;
-        if (col_ok && iz + 1 < nloc)  // next plane's operands, in flight during this plane
-            load_pw3<MODE, KAHAN>(M, outv, off0 + (long long)(iz + 1) * plane_stride, shot, b, F, nxt_pw);
+        Pw3 cur_pw;  // this plane's operands, in flight during the ring wait and the stencil
+        if (col_ok) load_pw3<MODE, KAHAN>(M, outv, off0 + (long long)iz * plane_stride, shot, b, F, cur_pw);
         if (col_ok && iz + kPrefetch3 < nloc)
             prefetch_pw3<MODE, KAHAN>(M, outv, off0 + (long long)(iz + kPrefetch3) * plane_stride, shot, b, F);
         // every plane up to k = iz + 8 must have landed
@@ -328,12 +328,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ 
     };
 
     // two planes per iteration: the operand bundles alternate roles instead of being copied
-    Pw3 pa, pb;
-    if (col_ok && nloc > 0) load_pw3<MODE, KAHAN>(M, outv, off0, shot, b, F, pa);
-    for (int iz = 0; iz < nloc; iz += 2) {
-        if (!plane(iz, pa, pb)) return;
-        if (iz + 1 < nloc && !plane(iz + 1, pb, pa)) return;
-    }
+#pragma unroll 2
+    for (int iz = 0; iz < nloc; ++iz)
+        if (!plane(iz)) return;
 }
 
 constexpr int kWs3Threads = kThreads + 32;  // eight consumer warps + one producer warp
