@@ -51,8 +51,8 @@ __device__ __forceinline__ void sponge_col3(const ModelStep3D& M, int y, int x, 
     A = make_float4(a[0], a[1], a[2], a[3]);
 }
 
-// Pointwise operands of one plane of a thread's 4 cells, loaded one plane ahead of their use
-// so that their HBM latency overlaps the previous plane's work.
+// Pointwise operands of one plane of a thread's 4 cells, loaded at the top of that plane (after an
+// L2 prefetch kPrefetch3 planes earlier) so that their latency overlaps the ring wait and the taps.
 struct Pw3 {
     float4 s, prev, d, dm, img, cmp;
 };
@@ -197,7 +197,7 @@ __device__ __forceinline__ void cells3(const ModelStep3D& M, const float* smem, 
         }
         st4(ip, iv);
     }
-    }
+}
 
 template <int MODE, bool KAHAN>
 __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ StepParams3D p) {
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ 
         return true;
     };
 
-    // two planes per iteration: the operand bundles alternate roles instead of being copied
+    // unrolled by two: the next plane's loads can then be scheduled into this plane's work
 #pragma unroll 2
     for (int iz = 0; iz < nloc; ++iz)
         if (!plane(iz)) return;
