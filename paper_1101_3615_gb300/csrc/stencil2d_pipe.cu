@@ -610,13 +610,12 @@ int occupancy(const void* fn, size_t smem) {
 }
 
 int num_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    static const int n = [] {  // initialised once, thread-safe (function-local static)
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n < 1) n = 1;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v < 1 ? 1 : v;
+    }();
     return n;
 }
 

@@ -463,12 +463,9 @@ __global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_const
 template <int MODE>
 static cudaError_t launch3_ws(const StepParams3D& p, dim3 grid, cudaStream_t st) {
     const size_t sm = (size_t)kRing * kPlaneBytes3;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step3d_ws<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // set on every launch (a host-side attribute, no stream work): no shared state between threads
+    cudaError_t e = cudaFuncSetAttribute(k_step3d_ws<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
     k_step3d_ws<MODE><<<grid, kWs3Threads, sm, st>>>(p);
     return cudaGetLastError();
 }
@@ -476,12 +473,8 @@ static cudaError_t launch3_ws(const StepParams3D& p, dim3 grid, cudaStream_t st)
 template <int MODE, bool KAHAN>
 static cudaError_t launch3(const StepParams3D& p, dim3 grid, cudaStream_t st) {
     const size_t sm = step3d_smem_bytes();
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step3d<MODE, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_step3d<MODE, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
     k_step3d<MODE, KAHAN><<<grid, kThreads, sm, st>>>(p);
     return cudaGetLastError();
 }
