@@ -2,8 +2,10 @@
 
 Each case patches one plausible error into the oracle -- a wrong stencil
 weight, a dropped 1/h^d source scaling, a flipped Born-source sign, an
-off-by-one time index in the imaging condition -- and checks that the
-closed-form or invariant pin that guards that part of the oracle fails.
+off-by-one time index in the imaging condition, a sponge whose damping sign
+is flipped, an adjoint that injects the residual at the wrong receivers --
+and checks that the closed-form or invariant pin that guards that part of the
+oracle fails.
 """
 import numpy as np
 import pytest
@@ -11,6 +13,7 @@ import pytest
 import oracle.wave as ow
 from analytic import green2d_trace, ricker_fn
 from oracle.fd import laplacian
+from wave_checks import sponge_reflection
 from workloads import mini_config
 
 C, F0, T0 = 2000.0, 15.0, 1.5 / 15.0
@@ -76,3 +79,20 @@ def test_imaging_time_index_shift_is_caught(monkeypatch):
             prev = d
     monkeypatch.setattr(ow.Problem, "_dtt_segments", shifted)
     assert _dot_mismatch() > 1e-4
+
+
+def test_flipped_sponge_damping_is_caught():
+    class Flipped(ow.Problem):
+        def __init__(self, *a, **k):
+            super().__init__(*a, **k)
+            self.am = 1.0 + 0.5 * self.dt * self.eta     # a- = 1 + eta dt / 2: no damping
+    assert sponge_reflection(Flipped) > 0.5
+
+
+def test_misplaced_adjoint_injection_is_caught(monkeypatch):
+    orig = ow.Problem._inject_adjoint
+
+    def inject(self, lam, r_n):
+        orig(self, lam, np.asarray(r_n)[..., ::-1])      # receiver order reversed
+    monkeypatch.setattr(ow.Problem, "_inject_adjoint", inject)
+    assert _dot_mismatch() > 1e-3
