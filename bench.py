@@ -52,8 +52,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-history", action="store_true",
                     help="skip the extra measurement with the full Dtt history resident")
-    ap.add_argument("--snapshot", default="fp16", choices=["fp32", "bf16", "fp16"],
-                    help="checkpoint storage of the batched path (default: FP16 with per-plane scale)")
+    ap.add_argument("--snapshot", default=None, choices=["fp32", "bf16", "fp16"],
+                    help="checkpoint storage of the batched path (default: the configuration's own, "
+                         "BF16 for configuration 5, else FP16; 16-bit planes carry a per-plane scale)")
     ap.add_argument("--profile", default=None, choices=["fwd", "adj"],
                     help="run only F (fwd) or F* (adj) once after one warm-up call: the small "
                          "command used for ncu captures of one kernel")
@@ -67,7 +68,10 @@ def parse():
     ap.add_argument("--fixed", default="",
                     help="pf,pa,R,G: fixed forward / adjoint kernel variants, rows per thread and shots "
                          "per adjoint CTA instead of the autotuner (for runs under a profiler)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.snapshot is None:
+        a.snapshot = "bf16" if a.config == 5 else "fp16"
+    return a
 
 
 def profile_run(a, wl):
@@ -634,6 +638,10 @@ def main():
                          "hv_vs_oracle": "see tests/test_gpu_parity.py (1e-4 FP32, 2e-3 16-bit)"},
         "cpu_baseline": cpu,
     }
+    if len(wl.shape) == 3:  # the 2D kernel choices do not apply: 3D has one kernel per step kind
+        for k in ("shot_group", "tile_z", "pipeline_forward", "pipeline_adjoint"):
+            line["config"].pop(k, None)
+        line["config"]["kernels"] = "k_step3d_ws (forward modes), k_step3d<ADJ> (adjoint + imaging)"
     if rank == 0:
         print(json.dumps(line))
     if dist:
