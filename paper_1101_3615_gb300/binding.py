@@ -64,6 +64,7 @@ def _load():
     sig = {
         "probe_create": (I, [C.POINTER(P), C.POINTER(probe_grid), VP, I, VP, I, VP, VP, I, D]),
         "probe_apply_F": (I, [P, VP, VP, I, VP]),
+        "probe_apply_F_noalloc": (I, [P, VP, VP, I, VP]),
         "probe_apply_Fadj": (I, [P, VP, VP, I, VP]),
         "probe_apply_H": (I, [P, VP, VP, I, VP]),
         "probe_apply_H_group": (I, [C.POINTER(P), I, C.POINTER(VP), C.POINTER(VP), C.POINTER(I), VP]),
@@ -92,6 +93,7 @@ lib = _load()
 # --- low-level functions with the C names -----------------------------------------
 probe_create = lib.probe_create
 probe_apply_F = lib.probe_apply_F
+probe_apply_F_noalloc = lib.probe_apply_F_noalloc
 probe_apply_Fadj = lib.probe_apply_Fadj
 probe_apply_H = lib.probe_apply_H
 probe_apply_H_group = lib.probe_apply_H_group
@@ -247,6 +249,16 @@ class Probe:
         a, ka = _ptr(dm)
         b, kb = _ptr(out)
         _check(lib.probe_apply_F(self.handle, a, b, nb, _stream(stream)), self.handle)
+        return out
+
+    def apply_F_noalloc(self, dm, out, stream=None):
+        """probe_apply_F_noalloc: dm and out must be CUDA tensors (the call allocates nothing)."""
+        if not (_is_torch(dm) and dm.is_cuda and _is_torch(out) and out.is_cuda):
+            raise ValueError("apply_F_noalloc takes CUDA tensors for dm and out")
+        nb = self._nb(dm, self.shape)
+        a, ka = _ptr(dm)
+        b, kb = _ptr(out)
+        _check(lib.probe_apply_F_noalloc(self.handle, a, b, nb, _stream(stream)), self.handle)
         return out
 
     def apply_Fadj(self, d, out=None, stream=None):

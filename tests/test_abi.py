@@ -107,3 +107,15 @@ def test_binding_stats_struct_matches_the_header():
     fields = re.findall(r"^\s*(double|long long|int)\s+(\w+);", body, re.M)
     ctype = {"double": C.c_double, "long long": C.c_longlong, "int": C.c_int}
     assert [(n, ctype[t]) for t, n in fields] == [(n, t) for n, t in probe_stats._fields_]
+
+
+def test_binding_names_every_declared_function(built_lib):
+    """The binding exposes each C entry point of the header under its C name, with its
+    argument types declared (one argtype per header parameter)."""
+    head = _header()
+    for name in declared_functions():
+        fn = getattr(built_lib, name, None)
+        assert fn is not None, f"binding lacks {name}"
+        m = re.search(r"^(?:probe_status|const char\*|void)\s+" + name + r"\s*\(([^)]*)\)", head, re.M)
+        params = [p for p in m.group(1).split(",") if p.strip() and p.strip() != "void"]
+        assert fn.argtypes is not None and len(fn.argtypes) == len(params), (name, params)
