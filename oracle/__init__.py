@@ -17,6 +17,9 @@ wave    discrete nonlinear forward map, Born operator F (Sec. 2 equations),
         operator H = F*F stacked over shots, and the misfit gradient.
 symbol  elementary operators B_i of the symbol expansion (Eq. compr2), the
         randomized least-squares fit of Sec. 1.4 and the preconditioner apply.
+solve   iterative solution of the linearised least-squares problem (gradient
+        descent, optionally preconditioned; conjugate gradients on the normal
+        equations) and the Krylov trial functions, as Sec. 2 compares them.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against closed forms, invariants or brute force (see ``tests/test_oracle_*``).
