@@ -210,6 +210,27 @@ probe_status probe_apply_precond(probe_t h, const probe_basis* basis,
                                  const double* coeffs, const float* img, float* out,
                                  probe_stream_t stream);
 
+/* Iterative solution of the linearised least-squares problem
+ * min 1/2 ||F dm - d||^2 through its normal equations H dm = F*d (Sec. 2: the
+ * fitted preconditioners are judged against gradient-descent iterations on
+ * this functional, and preconditioned iterations apply the approximate inverse
+ * to the migrated residual F*(d - F dm_k)).  rhs [n...] is the migrated image
+ * F*d; x [n...] holds the start on entry (zeros allowed) and the last iterate
+ * on return.  method PROBE_SOLVE_GD: steepest descent with exact line search,
+ * step p.r / p.Hp along p = r_k, or along p = sum_i c_i B_i r_k when basis and
+ * coeffs [P] (host, FP64) are given; PROBE_SOLVE_CG: conjugate gradients
+ * (basis must be NULL).  r_k = rhs - H x_k is updated by the recurrence; its
+ * 2-norms for k = 0..done go to resid [iters + 1] (host, FP64, may be NULL) and
+ * the number of iterations performed to *done (may be NULL): fewer than iters
+ * when the residual or the curvature p.Hp reaches zero.  Each iteration is one
+ * probe_apply_H of one trial (plus one probe_apply_precond); inner products
+ * are FP64 sums of FP32 products, read back every iteration, so the call
+ * synchronises `stream`.  rhs and x may be host or device arrays. */
+typedef enum { PROBE_SOLVE_GD = 0, PROBE_SOLVE_CG = 1 } probe_solve_method;
+probe_status probe_solve(probe_t h, int method, int iters, const probe_basis* basis,
+                         const double* coeffs, const float* rhs, float* x, double* resid,
+                         int* done, probe_stream_t stream);
+
 /* Nonlinear prediction d = calF[m] (Sec. 1.1): the receiver traces of
  * m u_tt - Lap u = f_s for every shot; m [n...] interior (the sponge keeps the
  * values of m0), d [ns][nt][nr]. */

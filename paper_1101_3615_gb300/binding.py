@@ -20,6 +20,7 @@ PROBE_OK = 0
 STATUS = {0: "PROBE_OK", -1: "PROBE_ERR_ARG", -2: "PROBE_ERR_CUDA", -3: "PROBE_ERR_OOM",
           -4: "PROBE_ERR_TIMEOUT", -5: "PROBE_ERR_NONFINITE", -6: "PROBE_ERR_STATE"}
 SNAP = {"fp32": 0, "bf16": 1, "fp16": 2}
+SOLVE = {"gd": 0, "cg": 1}
 OPT = {"check_finite": 1, "shot_wave": 2, "shot_group": 3, "use_graph": 4, "timing": 5, "tile_z": 6,
        "pipeline": 7, "dtt_history": 8, "autotune": 9, "pipe_rows": 10, "pipeline_adj": 11, "pipe_rows_adj": 12}
 
@@ -70,6 +71,7 @@ def _load():
         "probe_apply_H_group": (I, [C.POINTER(P), I, C.POINTER(VP), C.POINTER(VP), C.POINTER(I), VP]),
         "probe_fit": (I, [P, C.POINTER(probe_basis), VP, VP, I, VP, VP, VP]),
         "probe_apply_precond": (I, [P, C.POINTER(probe_basis), VP, VP, VP, VP]),
+        "probe_solve": (I, [P, I, I, C.POINTER(probe_basis), VP, VP, VP, VP, VP, VP]),
         "probe_forward_nonlinear": (I, [P, VP, VP, VP]),
         "probe_gradient": (I, [P, VP, VP, VP, VP]),
         "probe_set_option": (I, [P, I, C.c_longlong]),
@@ -99,6 +101,7 @@ probe_apply_H = lib.probe_apply_H
 probe_apply_H_group = lib.probe_apply_H_group
 probe_fit = lib.probe_fit
 probe_apply_precond = lib.probe_apply_precond
+probe_solve = lib.probe_solve
 probe_forward_nonlinear = lib.probe_forward_nonlinear
 probe_gradient = lib.probe_gradient
 probe_set_option = lib.probe_set_option
@@ -311,6 +314,26 @@ class Probe:
         b, kb = _ptr(out)
         _check(lib.probe_apply_precond(self.handle, C.byref(bs), c, a, b, _stream(stream)), self.handle)
         return out
+
+    def solve(self, rhs, iters, method="cg", x0=None, basis: Basis = None, coeffs=None, stream=None):
+        """probe_solve: iterate on H x = rhs (rhs = F*d).  Returns (x, resid, done): the last
+        iterate (same side as rhs), the residual norms ||rhs - H x_k|| for k = 0..done, and the
+        number of iterations performed."""
+        if x0 is None:
+            x = _empty_like_io(rhs, self.shape)
+            x[...] = 0
+        else:
+            x = x0.clone() if _is_torch(x0) else np.array(x0, dtype=np.float32)
+        resid = np.zeros(int(iters) + 1, dtype=np.float64)
+        done = C.c_int(0)
+        bs = basis.c_struct() if basis is not None else None
+        c, kc = _ptr(coeffs, np.float64) if coeffs is not None else (None, None)
+        a, ka = _ptr(rhs)
+        b, kb = _ptr(x)
+        _check(lib.probe_solve(self.handle, SOLVE[method], int(iters), C.byref(bs) if bs is not None else None,
+                               c, a, b, C.c_void_p(resid.ctypes.data), C.byref(done), _stream(stream)),
+               self.handle)
+        return x, resid[:done.value + 1], done.value
 
 
 def apply_H_group(probes, dms, outs=None, stream=None):

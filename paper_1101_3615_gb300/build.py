@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libprobe.so")
-SOURCES = ["probe_api.cu", "stencil2d.cu", "stencil2d_pipe.cu", "stencil3d.cu", "aux.cu", "fit.cu"]
+SOURCES = ["probe_api.cu", "stencil2d.cu", "stencil2d_pipe.cu", "stencil3d.cu", "aux.cu", "fit.cu", "solve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
