@@ -20,6 +20,8 @@ symbol  elementary operators B_i of the symbol expansion (Eq. compr2), the
 solve   iterative solution of the linearised least-squares problem (gradient
         descent, optionally preconditioned; conjugate gradients on the normal
         equations) and the Krylov trial functions, as Sec. 2 compares them.
+spectrum dense assembly of a model-space operator (brute force) and its
+        epsilon-rank, the quantity Sec. 2 tabulates for its Hessian.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against closed forms, invariants or brute force (see ``tests/test_oracle_*``).
