@@ -532,7 +532,7 @@ extern "C" probe_status probe_fit(probe_t h, const probe_basis* basis, const flo
     if (!h->fit) h->fit = new FitCache();
     FitCache& c = *h->fit;
     DevBuf ystage, xstage;
-    const float *yd, *xd;
+    const float *yd = nullptr, *xd = nullptr;
     probe_status s = PROBE_OK;
     do {
         if ((s = stage_f32(h, y, (size_t)p * B.npts, ystage, &yd, st)) != PROBE_OK) break;
@@ -598,7 +598,7 @@ extern "C" probe_status probe_apply_precond(probe_t h, const probe_basis* basis,
     if (!h->fit) h->fit = new FitCache();
     FitCache& c = *h->fit;
     DevBuf istage, ostage;
-    const float* id;
+    const float* id = nullptr;
     probe_status s = PROBE_OK;
     const bool host_out = !is_device_ptr(out);
     do {

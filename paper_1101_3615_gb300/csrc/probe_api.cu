@@ -1598,7 +1598,7 @@ extern "C" probe_status probe_apply_F(probe_t h, const float* dm, float* d, int 
     if (!dm || !d) return fail(h, PROBE_ERR_ARG, "NULL array");
     cudaStream_t st = (cudaStream_t)stream;
     bool hin = false;
-    const float* dmd;
+    const float* dmd = nullptr;
     TRY(stage_input(h, dm, (size_t)nb * h->nmodel, h->stage_in, &dmd, st, &hin));
     const size_t nd = (size_t)nb * h->ns * h->nt * h->nr;
     const bool hout = !is_device_ptr(d);
@@ -1623,7 +1623,7 @@ extern "C" probe_status probe_apply_Fadj(probe_t h, const float* d, float* img, 
     if (!d || !img) return fail(h, PROBE_ERR_ARG, "NULL array");
     cudaStream_t st = (cudaStream_t)stream;
     bool hin = false;
-    const float* dd;
+    const float* dd = nullptr;
     const size_t nd = (size_t)nb * h->ns * h->nt * h->nr;
     TRY(stage_input(h, d, nd, h->stage_in, &dd, st, &hin));
     const bool hout = !is_device_ptr(img);
@@ -1648,7 +1648,7 @@ extern "C" probe_status probe_apply_H(probe_t h, const float* dm, float* Hdm, in
     if (!dm || !Hdm) return fail(h, PROBE_ERR_ARG, "NULL array");
     cudaStream_t st = (cudaStream_t)stream;
     bool hin = false;
-    const float* dmd;
+    const float* dmd = nullptr;
     TRY(stage_input(h, dm, (size_t)nb * h->nmodel, h->stage_in, &dmd, st, &hin));
     const bool hout = !is_device_ptr(Hdm);
     float* o = Hdm;
@@ -1670,7 +1670,7 @@ extern "C" probe_status probe_forward_nonlinear(probe_t h, const float* m, float
     if (!m || !d) return fail(h, PROBE_ERR_ARG, "NULL array");
     cudaStream_t st = (cudaStream_t)stream;
     bool hin = false;
-    const float* md;
+    const float* md = nullptr;
     TRY(stage_input(h, m, (size_t)h->nmodel, h->stage_in, &md, st, &hin));
     const size_t nd = (size_t)h->ns * h->nt * h->nr;
     const bool hout = !is_device_ptr(d);
@@ -1699,8 +1699,8 @@ extern "C" probe_status probe_gradient(probe_t h, const float* m, const float* r
     if (!m || !resid || !g) return fail(h, PROBE_ERR_ARG, "NULL array");
     cudaStream_t st = (cudaStream_t)stream;
     bool hin1 = false;
-    const float* md;
-    const float* rd;
+    const float* md = nullptr;
+    const float* rd = nullptr;
     // stage the model in stage_out's spare room is not possible; use two buffers
     const size_t nd = (size_t)h->ns * h->nt * h->nr;
     TRY(stage_input(h, resid, nd, h->stage_in, &rd, st, &hin1));
@@ -1774,7 +1774,7 @@ extern "C" probe_status probe_apply_H_group(const probe_t* models, int nmodels, 
     for (int k = 0; k < nmodels; ++k) {
         probe_t h = models[k];
         bool hin = false;
-        const float* dmd;
+        const float* dmd = nullptr;
         TRY(stage_input(h, dm[k], (size_t)nb[k] * h->nmodel, h->stage_in, &dmd, st, &hin));
         host_out[k] = !is_device_ptr(Hdm[k]);
         outs[k] = Hdm[k];
