@@ -3,8 +3,10 @@
 Each case patches one plausible error into the oracle -- a wrong stencil
 weight, a dropped 1/h^d source scaling, a flipped Born-source sign, an
 off-by-one time index in the imaging condition, a sponge whose damping sign
-is flipped, an adjoint that injects the residual at the wrong receivers --
-and checks that the closed-form or invariant pin that guards that part of the
+is flipped, an adjoint that injects the residual at the wrong receivers, a
+flipped rational-Chebyshev map, a wrong sign of the symbol order or of a sine
+harmonic, a wrong spatial-mode period, a fit with its pairs swapped -- and
+checks that the closed-form or invariant pin that guards that part of the
 oracle fails.
 """
 import numpy as np
@@ -96,3 +98,75 @@ def test_misplaced_adjoint_injection_is_caught(monkeypatch):
         orig(self, lam, np.asarray(r_n)[..., ::-1])      # receiver order reversed
     monkeypatch.setattr(ow.Problem, "_inject_adjoint", inject)
     assert _dot_mismatch() > 1e-3
+
+
+# -- the symbol expansion and the fit: each planted mistake must make one of the pins in
+#    test_oracle_symbol.py fail (they are called here as plain functions).
+import oracle.symbol as osym
+import test_oracle_symbol as sym_pins
+
+
+def _mutated_multiplier(t_sign=1.0, exp_sign=1.0):
+    def multiplier(self, a, q):
+        kvec = self._kgrid()
+        knorm = np.sqrt(sum(k ** 2 for k in kvec))
+        pos = (knorm > 0) & ~self._nyquist_mask()
+        safe = np.where(knorm > 0, knorm, 1.0)
+        t = t_sign * (safe - self.L) / (safe + self.L)
+        cheb = np.cos(q * np.arccos(np.clip(t, -1.0, 1.0)))
+        beta = self.angular_fn(a, kvec) * cheb * safe ** (exp_sign * self.order)
+        return np.where(pos, beta, 0.0)
+    return multiplier
+
+
+def test_unmutated_symbol_pins_pass():
+    sym_pins.test_plane_wave_eigenvalues_2d(-1.0)
+    sym_pins.test_spatial_modes_multiply()
+    sym_pins.test_exact_recovery_of_known_expansion()
+
+
+def test_flipped_chebyshev_map_is_caught(monkeypatch):
+    monkeypatch.setattr(osym.Basis, "multiplier", _mutated_multiplier(t_sign=-1.0))
+    with pytest.raises(AssertionError):
+        sym_pins.test_plane_wave_eigenvalues_2d(-1.0)
+
+
+def test_wrong_symbol_order_sign_is_caught(monkeypatch):
+    monkeypatch.setattr(osym.Basis, "multiplier", _mutated_multiplier(exp_sign=-1.0))
+    with pytest.raises(AssertionError):
+        sym_pins.test_plane_wave_eigenvalues_2d(-1.0)
+
+
+def test_wrong_sine_harmonic_sign_is_caught(monkeypatch):
+    orig = osym.Basis.angular_fn
+
+    def angular_fn(self, a, kvec):
+        f = orig(self, a, kvec)
+        return -f if self.ndim == 2 and self.angular[a] < 0 else f    # sin(q theta) for q < 0
+    monkeypatch.setattr(osym.Basis, "angular_fn", angular_fn)
+    with pytest.raises(AssertionError):
+        sym_pins.test_plane_wave_eigenvalues_2d(-1.0)
+
+
+def test_wrong_spatial_period_is_caught(monkeypatch):
+    def spatial_mode(self, lam):
+        out = np.ones(self.shape)
+        for ax, k in enumerate(self.spatial[lam]):
+            n = self.shape[ax]
+            i = np.arange(n, dtype=np.float64)
+            f = np.ones(n) if k == 0 else (np.cos(2 * np.pi * k * i / (n + 1)) if k > 0
+                                           else np.sin(2 * np.pi * (-k) * i / (n + 1)))
+            sh = [1] * self.ndim
+            sh[ax] = n
+            out = out * f.reshape(sh)
+        return out
+    monkeypatch.setattr(osym.Basis, "spatial_mode", spatial_mode)
+    with pytest.raises(AssertionError):
+        sym_pins.test_spatial_modes_multiply()
+
+
+def test_fit_with_swapped_pairs_is_caught(monkeypatch):
+    orig = osym.fit
+    monkeypatch.setattr(sym_pins, "fit", lambda basis, y, x: orig(basis, x, y))
+    with pytest.raises(AssertionError):
+        sym_pins.test_exact_recovery_of_known_expansion()
