@@ -211,12 +211,23 @@ cudaError_t launch_check_finite(const float* a, long long n, int* err, cudaStrea
 
 // ---- checkpoint codec ------------------------------------------------------
 // A checkpoint holds, per shot, the leapfrog state (u^n, u^{n-1}).  In 16-bit
-// storage it is kept as q0 = u^n and q1 = u^n - u^{n-1}, each plane with its
-// own absmax scale: the time difference is much smaller than u itself, so
+// storage it is kept as q0 = u^n and q1 = u^n - u^{n-1}, each with its own
+// absmax scale: the time difference is much smaller than u itself, so
 // quantising it separately keeps the restored state's time derivative accurate
 // (independent rounding of u^n and u^{n-1} would leave an error of the size of
 // u's rounding in their difference).  State plane 2j + pc holds u^n of shot j,
 // plane 2j + (1 - pc) holds u^{n-1}.
+//
+// Storage planes per shot: FP16 keeps q0 and q1 (2 planes).  BF16 keeps q0 as
+// the unevaluated sum of two BF16 numbers hi + lo (lo = the BF16 rounding of
+// q0 - hi) and q1 as one (3 planes).  The reason: one BF16 number carries 8
+// significant bits, and the rounding error of the restored position plane is
+// white at the grid scale, where the 8th-order Laplacian multiplies it by up to
+// sum|w_k| / h^2 per axis -- about 15 times the Dtt u of a field sampled at ten
+// points per wavelength -- in every recomputed step of the segment.  With a
+// single BF16 position plane the imaging result is off by about 1e-2; the
+// two-term position plane (16 significant bits) leaves the rounding of q1,
+// which is 10-20 times smaller in absolute size, as the dominant term.
 __device__ __forceinline__ float ckpt_value(const float* __restrict__ state, long long F, int plane,
                                             int pc, long long i) {
     const int shot = plane >> 1;
@@ -247,25 +258,39 @@ __device__ __forceinline__ float ckpt_scale(float amax, int dtype) {
     return dtype == PROBE_SNAP_FP16 ? amax * (1.0f / 16384.0f) : amax;
 }
 
+__host__ __device__ constexpr int ckpt_store_planes(int dtype) {
+    return dtype == PROBE_SNAP_BF16 ? 3 : 2;
+}
+
+size_t ckpt_bytes_per_shot(int dtype, long long F) {
+    return (size_t)ckpt_store_planes(dtype) * (size_t)F * (dtype == PROBE_SNAP_FP32 ? 4u : 2u);
+}
+
+// blockIdx.y = logical plane (2 j + 0: q0 of shot j, 2 j + 1: q1).
 __global__ void k_encode(const float* __restrict__ state, long long F, int pc, void* dst,
                          const float* __restrict__ absmax, float* scales, int dtype) {
     const int plane = blockIdx.y;
+    const int shot = plane >> 1, which = plane & 1;
     const float sc = ckpt_scale(absmax[plane], dtype);
     const float inv = 1.0f / sc;
     if (blockIdx.x == 0 && threadIdx.x == 0) scales[plane] = sc;
+    const long long base = (long long)shot * ckpt_store_planes(dtype) * F;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < F;
          i += (long long)gridDim.x * blockDim.x) {
-        const float v = ckpt_value(state, F, plane, pc, i) * inv;
-        if (dtype == PROBE_SNAP_FP16)
-            reinterpret_cast<__half*>(dst)[(long long)plane * F + i] = __float2half_rn(v);
-        else
-            reinterpret_cast<__nv_bfloat16*>(dst)[(long long)plane * F + i] = __float2bfloat16_rn(v);
+        const float v = __fmul_rn(ckpt_value(state, F, plane, pc, i), inv);
+        if (dtype == PROBE_SNAP_FP16) {
+            reinterpret_cast<__half*>(dst)[base + which * F + i] = __float2half_rn(v);
+        } else {
+            __nv_bfloat16* q = reinterpret_cast<__nv_bfloat16*>(dst) + base;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            if (which == 0) {
+                q[i] = hi;  // v - hi is exact in FP32
+                q[F + i] = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(hi)));
+            } else {
+                q[2 * F + i] = hi;
+            }
+        }
     }
-}
-
-__device__ __forceinline__ float ckpt_load(const void* src, int dtype, long long j) {
-    if (dtype == PROBE_SNAP_FP16) return __half2float(reinterpret_cast<const __half*>(src)[j]);
-    return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(src)[j]);
 }
 
 // blockIdx.y = shot: restores u^n into plane 2j + pc and u^{n-1} into 2j + (1 - pc).
@@ -273,12 +298,23 @@ __global__ void k_decode(const void* src, const float* __restrict__ scales, long
                          int pc, float* __restrict__ state) {
     const int shot = blockIdx.y;
     const float s0 = scales[2 * shot], s1 = scales[2 * shot + 1];
+    const long long base = (long long)shot * ckpt_store_planes(dtype) * F;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < F;
          i += (long long)gridDim.x * blockDim.x) {
-        const float un = ckpt_load(src, dtype, (long long)(2 * shot) * F + i) * s0;
-        const float du = ckpt_load(src, dtype, (long long)(2 * shot + 1) * F + i) * s1;
+        float q0, q1;
+        if (dtype == PROBE_SNAP_FP16) {
+            const __half* q = reinterpret_cast<const __half*>(src) + base;
+            q0 = __half2float(q[i]);
+            q1 = __half2float(q[F + i]);
+        } else {
+            const __nv_bfloat16* q = reinterpret_cast<const __nv_bfloat16*>(src) + base;
+            q0 = __fadd_rn(__bfloat162float(q[i]), __bfloat162float(q[F + i]));  // exact: 17 bits
+            q1 = __bfloat162float(q[2 * F + i]);
+        }
+        const float un = __fmul_rn(q0, s0);
+        const float du = __fmul_rn(q1, s1);
         state[(long long)(2 * shot + pc) * F + i] = un;
-        state[(long long)(2 * shot + (pc ^ 1)) * F + i] = un - du;
+        state[(long long)(2 * shot + (pc ^ 1)) * F + i] = __fsub_rn(un, du);
     }
 }
 

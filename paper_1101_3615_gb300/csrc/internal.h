@@ -182,6 +182,8 @@ cudaError_t launch_check_finite(const float* a, long long n, int* err, cudaStrea
 cudaError_t launch_build_injection(const float* rdata, long long dss, long long dts, int nr, int n_hi, int nsteps,
                                    int nshots, int nb, int nuc, const int* uc_ptr, const int* uc_rec,
                                    const int* uc_pos, float* inj, long long block, cudaStream_t st);
+// Checkpoint storage of one shot (FP32: 2 planes; FP16: 2 half planes; BF16: 3 bf16 planes).
+size_t ckpt_bytes_per_shot(int dtype, long long F);
 // pc = plane parity of u^n (u^{n-1} is in the other plane of each shot).
 cudaError_t launch_encode_ckpt(const float* state, int nplanes, long long F, int pc, void* dst,
                                float* scales, int dtype, float* absmax_scratch, cudaStream_t st);

@@ -148,7 +148,6 @@ void free_ws(Workspace& w) {
     w.generation = ++g_generation;
 }
 
-size_t snap_bytes(int snap) { return snap == PROBE_SNAP_FP32 ? 4 : 2; }
 
 // Bytes per resident shot and fixed bytes of a job with nb trials.
 bool use_history(probe_t h, int with_ckpt) { return with_ckpt && h->opt_dtt_history && h->ndim == 2; }
@@ -159,7 +158,7 @@ void ws_bytes(probe_t h, int nb, int with_ckpt, int with_data, double* per_shot,
     if (use_history(h, with_ckpt))
         ps += (double)(h->nt - 1) * F4;
     else if (with_ckpt)
-        ps += (double)h->nck * 2 * h->F * snap_bytes(h->snap) + (double)h->K * F4 + 16.0 * h->nck;
+        ps += (double)h->nck * ckpt_bytes_per_shot(h->snap, h->F) + (double)h->K * F4 + 16.0 * h->nck;
     if (with_data) ps += (double)nb * h->nt * h->nr * 4.0;
     if (h->ndim == 3 && with_ckpt) ps += 2.0 * nb * F4;  // per-shot images + compensation
     *per_shot = ps;
@@ -228,7 +227,7 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     if (history) {
         TRY(alloc((void**)&w.dtt, (size_t)W * (h->nt - 1) * F * 4));  // Dtt u^n of every step
     } else if (with_ckpt) {
-        TRY(alloc(&w.ckpt, (size_t)h->nck * W * 2 * F * snap_bytes(h->snap)));
+        TRY(alloc(&w.ckpt, (size_t)h->nck * W * ckpt_bytes_per_shot(h->snap, F)));
         TRY(alloc((void**)&w.scales, (size_t)h->nck * W * 2 * 4));
         TRY(alloc((void**)&w.absmax, (size_t)W * 2 * 4));
         TRY(alloc((void**)&w.dtt, (size_t)W * h->K * F * 4));
@@ -583,8 +582,8 @@ probe_status run_forward(Sweep& sw, FwdKind kind, bool ckpt) {
             for (Job& jb : sw.jobs) {
                 Workspace& w = jb.h->ws;
                 const int k = n / sw.K;
-                const size_t per = (size_t)jb.W * 2 * jb.h->F;
-                void* dst = (char*)w.ckpt + (size_t)k * per * snap_bytes(jb.h->snap);
+                const size_t per = (size_t)jb.W * ckpt_bytes_per_shot(jb.h->snap, jb.h->F);
+                void* dst = (char*)w.ckpt + (size_t)k * per;
                 cudaError_t e = launch_encode_ckpt(w.u, jb.W * 2, jb.h->F, n & 1, dst,
                                                    w.scales + (size_t)k * jb.W * 2, jb.h->snap, w.absmax, sw.st);
                 if (e != cudaSuccess) return cuda_fail(jb.h, e, "checkpoint store");
@@ -659,8 +658,8 @@ probe_status run_adjoint(Sweep& sw) {
         record(h0, ev++, sw.st);
         for (Job& jb : sw.jobs) {
             Workspace& w = jb.h->ws;
-            const size_t per = (size_t)jb.W * 2 * jb.h->F;
-            const void* src = (const char*)w.ckpt + (size_t)k * per * snap_bytes(jb.h->snap);
+            const size_t per = (size_t)jb.W * ckpt_bytes_per_shot(jb.h->snap, jb.h->F);
+            const void* src = (const char*)w.ckpt + (size_t)k * per;
             cudaError_t e = launch_decode_ckpt(src, w.scales + (size_t)k * jb.W * 2, jb.W * 2, jb.h->F, k0 & 1,
                                                jb.h->snap, w.u, sw.st);
             if (e != cudaSuccess) return cuda_fail(jb.h, e, "checkpoint restore");
@@ -778,8 +777,8 @@ probe_status run_forward3d(const Job& jb, FwdKind kind, bool ckpt, cudaStream_t 
     for (int n = 0; n < h->nt - 1; ++n) {
         if (ckpt && n % h->K == 0) {
             const int k = n / h->K;
-            const size_t per = (size_t)jb.W * 2 * h->F;
-            void* dst = (char*)w.ckpt + (size_t)k * per * snap_bytes(h->snap);
+            const size_t per = (size_t)jb.W * ckpt_bytes_per_shot(h->snap, h->F);
+            void* dst = (char*)w.ckpt + (size_t)k * per;
             cudaError_t e = launch_encode_ckpt(w.u, jb.W * 2, h->F, n & 1, dst, w.scales + (size_t)k * jb.W * 2,
                                                h->snap, w.absmax, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint store");
@@ -829,8 +828,8 @@ probe_status run_adjoint3d(const Job& jb, cudaStream_t st, Count3& c) {
         const int k1 = std::min(k0 + h->K, h->nt - 1);
         if (k0 >= k1) continue;
         record(h, ev++, st);
-        const size_t per = (size_t)jb.W * 2 * h->F;
-        const void* src = (const char*)w.ckpt + (size_t)k * per * snap_bytes(h->snap);
+        const size_t per = (size_t)jb.W * ckpt_bytes_per_shot(h->snap, h->F);
+        const void* src = (const char*)w.ckpt + (size_t)k * per;
         cudaError_t e = launch_decode_ckpt(src, w.scales + (size_t)k * jb.W * 2, jb.W * 2, h->F, k0 & 1, h->snap, w.u,
                                            st);
         if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint restore");

@@ -74,7 +74,8 @@ def test_forward_kernels_3d_agree(cuda_device, small3d):
         assert rel(out[1][1][b].cpu().numpy(), hes[b]) < 1e-4
 
 
-@pytest.mark.parametrize("snap,tol,wave", [("fp32", 1e-4, 0), ("fp32", 1e-4, 3), ("fp16", 2e-3, 0)])
+@pytest.mark.parametrize("snap,tol,wave", [("fp32", 1e-4, 0), ("fp32", 1e-4, 3), ("fp16", 2e-3, 0),
+                                           ("bf16", 2e-3, 0), ("bf16", 2e-3, 3)])
 def test_hessian_3d(cuda_device, small3d, snap, tol, wave):
     wl, prob, born, hes = small3d
     p = make_probe(wl, snapshot_dtype=snap)

@@ -259,6 +259,24 @@ def test_config2_full_size_sampled_shots(cuda_device, cfg2, cfg2_oracle):
     assert rel(img, img5) < 1e-4
 
 
+@pytest.mark.parametrize("snap", ["fp16", "bf16"])
+def test_config2_full_size_16bit_vs_oracle(cuda_device, cfg2, cfg2_oracle, snap):
+    """The batched path the bench times (all 32 shots resident, 16-bit checkpoints, autotuned
+    kernels, CUDA graphs) at full size against the oracle: F* applied to shot 5's Born traces,
+    the other shots' data zero, is that shot's term F_5^T F_5 dm of H dm, which the oracle
+    computes alone; within the 16-bit bound."""
+    wl = cfg2
+    p = make_probe(wl, snapshot_dtype=snap)
+    p.set_option("use_graph", 1)
+    dm = dev(wl.trials)
+    d = p.apply_F(dm)
+    r = torch.zeros_like(d)
+    r[0, 5] = d[0, 5]
+    img = p.apply_Fadj(r).cpu().numpy()[0]
+    _, _, (_, img5) = cfg2_oracle.get(timeout=3000)
+    assert rel(img, img5) < 2e-3
+
+
 def test_config2_full_size_dot_and_hessian_consistency(cuda_device, cfg2):
     wl = cfg2
     p = make_probe(wl)
