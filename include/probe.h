@@ -107,7 +107,8 @@ typedef struct {
 typedef enum {
     PROBE_OPT_CHECK_FINITE = 1,  /* 1 (default): check inputs/outputs for NaN/Inf, sync */
     PROBE_OPT_SHOT_WAVE = 2,     /* max shots resident at once; 0 (default) = memory planner */
-    PROBE_OPT_SHOT_GROUP = 3,    /* shots per CTA in the adjoint sweep; 0 = autotuned */
+    PROBE_OPT_SHOT_GROUP = 3,    /* 2D: shots per CTA in the adjoint sweep; 3D: shots per adjoint cluster
+                                    (PROBE_OPT_CLUSTER3D bit 1); 0 = autotuned (2D) or 4 (3D) */
     PROBE_OPT_USE_GRAPH = 4,     /* 1 (default): replay sweeps from a captured CUDA graph */
     PROBE_OPT_TIMING = 5,        /* CUDA-event timings read by probe_get_stats (recorded on the call's
                                     stream, also inside replayed graphs; no call synchronises):
@@ -127,7 +128,16 @@ typedef enum {
     PROBE_OPT_PIPE_ROWS = 10,    /* 2D pipelined kernels: rows per thread R, tile 64 x 16R (1 or 2),
                                     forward and adjoint */
     PROBE_OPT_PIPELINE_ADJ = 11, /* 2D adjoint kernel only (0, 2 or 3; PROBE_OPT_PIPELINE sets both) */
-    PROBE_OPT_PIPE_ROWS_ADJ = 12 /* 2D pipelined adjoint only: rows per thread (1 or 2) */
+    PROBE_OPT_PIPE_ROWS_ADJ = 12, /* 2D pipelined adjoint only: rows per thread (1 or 2) */
+    PROBE_OPT_CLUSTER3D = 13     /* 3D thread-block-cluster kernels, a bit mask (default 0):
+                                    bit 0 (1): the incident and Born fields of a column tile advance in
+                                    one launch on a cluster of 1 + nb CTAs (nb <= 7), exchanging Dtt u0
+                                    through distributed shared memory instead of HBM;
+                                    bit 1 (2): the adjoint runs on clusters of PROBE_OPT_SHOT_GROUP shots
+                                    (1, 2, 4 or 8; 0 = 4) whose imaging terms are summed in shared
+                                    memory before one Kahan update of the group's image;
+                                    0 = one field per CTA and separate incident and Born launches (the
+                                    default: three CTAs per SM instead of two, measured faster) */
 } probe_option;
 
 /* Counters and timings of the last apply call (probe_get_stats). */
@@ -194,12 +204,15 @@ probe_status probe_apply_H_group(const probe_t* models, int nmodels,
 
 /* Randomized fit of Sec. 1.4: given trial functions y_j and x_j = H y_j
  * (j = 1..p, each [n...]), find the coefficients c (FP64, [P] with
- * P = nspatial * nangular * nradial) minimising
+ * P = nspatial * nangular * nradial <= 1024) minimising
  *     sum_j || y_j - sum_i c_i B_i x_j ||^2
- * by the normal equations M c = (Bx)^T y, M_ik = sum_j (B_i x_j)^T (B_k x_j),
- * formed and solved in FP64 on the device.  coeffs and resid_rel
- * (||y - Bx c|| / ||y||) are written to host memory; the call synchronises.
- * Returns PROBE_ERR_STATE if M is not numerically positive definite. */
+ * (the least-squares problem whose normal equations M c = (Bx)^T y,
+ * M_ik = sum_j (B_i x_j)^T (B_k x_j), Sec. 1.4 writes).  Solved on the device
+ * in FP64 through a QR factorisation of the stacked columns A = [B_i x_j]
+ * (CholeskyQR2: Cholesky QR with one reorthogonalisation), so the error grows
+ * like cond(A) eps, not cond(A)^2 eps.  coeffs (host or device) and resid_rel
+ * (||y - Bx c|| / ||y||, host) are written; the call synchronises.
+ * Returns PROBE_ERR_STATE if the columns are numerically rank deficient. */
 probe_status probe_fit(probe_t h, const probe_basis* basis, const float* y,
                        const float* Hy, int p, double* coeffs, double* resid_rel,
                        probe_stream_t stream);
@@ -231,6 +244,16 @@ probe_status probe_solve(probe_t h, int method, int iters, const probe_basis* ba
                          const double* coeffs, const float* rhs, float* x, double* resid,
                          int* done, probe_stream_t stream);
 
+/* Krylov trial functions of the Kn preconditioners (Sec. 2, the comparison of
+ * Krylov and randomized trial functions): y_1 = rhs / ||rhs|| (rhs normally the
+ * migrated data F*d), x_j = H y_j, y_{j+1} = x_j / ||x_j|| for j = 1..n.
+ * rhs [n_model]; y, Hy [n][n_model] receive the trials and their H
+ * applications, ready for probe_fit (pairs (y_j, x_j)).  Each step is one
+ * probe_apply_H of one trial; the norms are FP64 sums formed on the device.
+ * Arrays may be host or device memory; the call synchronises `stream`. */
+probe_status probe_krylov_trials(probe_t h, const float* rhs, int n, float* y, float* Hy,
+                                 probe_stream_t stream);
+
 /* Nonlinear prediction d = calF[m] (Sec. 1.1): the receiver traces of
  * m u_tt - Lap u = f_s for every shot; m [n...] interior (the sponge keeps the
  * values of m0), d [ns][nt][nr]. */
@@ -250,6 +273,7 @@ probe_status probe_gradient(probe_t h, const float* m, const float* resid, float
  * synchronise the device, a real-time loop).  This operation has no
  * counterpart in the paper; it is an engineering variant of probe_apply_F.
  * Create the handle once beforehand (probe_create allocates its model arrays).
+ * 2D handles only (a 3D handle gives PROBE_ERR_ARG).
  * dm [nb][n...] and d [nb][ns][nt][nr] must be device arrays.  The per-call
  * scratch is a library-internal static device array of 32 MiB, held on every
  * GPU that loads the library until the process exits; shots are processed in

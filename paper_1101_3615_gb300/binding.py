@@ -22,7 +22,8 @@ STATUS = {0: "PROBE_OK", -1: "PROBE_ERR_ARG", -2: "PROBE_ERR_CUDA", -3: "PROBE_E
 SNAP = {"fp32": 0, "bf16": 1, "fp16": 2}
 SOLVE = {"gd": 0, "cg": 1}
 OPT = {"check_finite": 1, "shot_wave": 2, "shot_group": 3, "use_graph": 4, "timing": 5, "tile_z": 6,
-       "pipeline": 7, "dtt_history": 8, "autotune": 9, "pipe_rows": 10, "pipeline_adj": 11, "pipe_rows_adj": 12}
+       "pipeline": 7, "dtt_history": 8, "autotune": 9, "pipe_rows": 10, "pipeline_adj": 11, "pipe_rows_adj": 12,
+       "cluster3d": 13}
 
 
 class probe_grid(C.Structure):
@@ -72,6 +73,7 @@ def _load():
         "probe_fit": (I, [P, C.POINTER(probe_basis), VP, VP, I, VP, VP, VP]),
         "probe_apply_precond": (I, [P, C.POINTER(probe_basis), VP, VP, VP, VP]),
         "probe_solve": (I, [P, I, I, C.POINTER(probe_basis), VP, VP, VP, VP, VP, VP]),
+        "probe_krylov_trials": (I, [P, VP, I, VP, VP, VP]),
         "probe_forward_nonlinear": (I, [P, VP, VP, VP]),
         "probe_gradient": (I, [P, VP, VP, VP, VP]),
         "probe_set_option": (I, [P, I, C.c_longlong]),
@@ -102,6 +104,7 @@ probe_apply_H_group = lib.probe_apply_H_group
 probe_fit = lib.probe_fit
 probe_apply_precond = lib.probe_apply_precond
 probe_solve = lib.probe_solve
+probe_krylov_trials = lib.probe_krylov_trials
 probe_forward_nonlinear = lib.probe_forward_nonlinear
 probe_gradient = lib.probe_gradient
 probe_set_option = lib.probe_set_option
@@ -334,6 +337,18 @@ class Probe:
                                c, a, b, C.c_void_p(resid.ctypes.data), C.byref(done), _stream(stream)),
                self.handle)
         return x, resid[:done.value + 1], done.value
+
+
+    def krylov_trials(self, rhs, n, stream=None):
+        """probe_krylov_trials: the Kn trial functions y_1 = rhs/||rhs||, y_{j+1} = H y_j/||H y_j||
+        and their H applications; returns (y, Hy), each [n, *shape] on the side of rhs."""
+        y = _empty_like_io(rhs, (int(n),) + self.shape)
+        x = _empty_like_io(rhs, (int(n),) + self.shape)
+        a, ka = _ptr(rhs)
+        b, kb = _ptr(y)
+        c, kc = _ptr(x)
+        _check(lib.probe_krylov_trials(self.handle, a, int(n), b, c, _stream(stream)), self.handle)
+        return y, x
 
 
 def apply_H_group(probes, dms, outs=None, stream=None):

@@ -354,6 +354,26 @@ cudaError_t launch_scale_copy(const float* src, float* dst, long long n, float a
     return cudaGetLastError();
 }
 
+__global__ void k_kahan_fold(float4* __restrict__ img, float4* __restrict__ comp, const float4* __restrict__ seg,
+                             long long n4) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+         i += (long long)gridDim.x * blockDim.x) {
+        float4 s = img[i], c = comp[i];
+        const float4 v = seg[i];
+        kahan4(s, c, v.x, v.y, v.z, v.w);
+        img[i] = s;
+        comp[i] = c;
+    }
+}
+
+cudaError_t launch_kahan_fold(float* img, float* comp, const float* seg, long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (n % 4) return cudaErrorInvalidValue;  // whole planes of a padded grid (pitch a multiple of 32)
+    k_kahan_fold<<<grid_for(n / 4), 256, 0, st>>>(reinterpret_cast<float4*>(img), reinterpret_cast<float4*>(comp),
+                                                   reinterpret_cast<const float4*>(seg), n / 4);
+    return cudaGetLastError();
+}
+
 // Diagnostic: one CTA waits on an mbarrier phase that nothing ever completes, so
 // the bounded wait can only end by its time limit; the kernel then records the
 // timeout in the device error word and returns (the context stays usable).

@@ -68,6 +68,51 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
+// ---- thread-block clusters: distributed shared memory and cluster-scope mbarriers ----
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Shared-memory address (shared::cta window) of this CTA -> the same offset in CTA `rank` of
+// the cluster (shared::cluster window).
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// Asynchronous store of 16 bytes into the shared memory of another CTA of the cluster; its
+// arrival decrements the transaction count of that CTA's mbarrier `remote_bar` by 16 bytes, so
+// the data and the signal travel together (no fence on the storing thread).
+__device__ __forceinline__ void st_async4(uint32_t remote_addr, const float4& v, uint32_t remote_bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     remote_addr),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(remote_bar)
+                 : "memory");
+}
+
+// Plain (relaxed) arrival on an mbarrier of another CTA of the cluster: used to hand a buffer
+// back once the values read from it have been consumed, so it orders nothing else and does not
+// wait for this thread's outstanding global stores.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t remote_bar) {
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote_bar) : "memory");
+}
+
+// Arm a local mbarrier for `bytes` of incoming asynchronous stores (one arrival, relaxed).
+__device__ __forceinline__ void mbar_arm_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.relaxed.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Cluster-wide barrier of all non-exited threads (release / acquire).  Used once after the
+// mbarrier initialisation (no remote arrival may precede it) and once before exit (no CTA may
+// leave while another can still touch its shared memory).
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
 // Rounding-explicit pieces of the explicit time update u^{n+1} = G (2 u^n - a- u^{n-1} + rhs)
 // (Sec. 2 scheme with the sponge).  Every product and sum is one IEEE operation written
 // out, so the compiler cannot fuse them differently in different kernel instantiations:

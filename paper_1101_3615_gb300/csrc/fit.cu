@@ -5,10 +5,22 @@
 // problem are (B_i x_j)(x) = alpha_lam(x) * IFFT[beta_m(k) FFT(x_j)](x),
 // i = (lam, m), m = (angular a, radial q).  One batched D2Z transform of the
 // p zero-padded trials, one multiply + batched Z2D transform per distinct k
-// multiplier beta_m, then the normal equations of Sec. 1.4,
-//     M_ik = sum_j (B_i x_j)^T (B_k x_j),   b_i = sum_j (B_i x_j)^T y_j,
-// accumulated in FP64 by a blocked Gram kernel and solved by an in-CTA
-// Cholesky factorisation; a second pass forms ||y - sum_i c_i B_i x|| / ||y||.
+// multiplier beta_m; then the least-squares problem min ||A c - y|| over the
+// rows of all trials is solved through a QR factorisation of A in FP64 by
+// CholeskyQR2 (Cholesky QR with one reorthogonalisation):
+//     pass 1:  A^T A = R1^T R1                       (Cholesky)
+//     pass 2:  Q1 = A R1^{-1} row by row, Q1^T Q1 = R2^T R2, z = Q1^T y
+//     A = Q R with Q = Q1 R2^{-1}, R = R2 R1:  c = R^{-1} Q^T y = R1^{-1} R2^{-1} R2^{-T} z.
+// The Gram matrix of the reorthogonalised Q1 is within a few units of round-off
+// of the identity whenever cond(A) is below about 1e7, so the solution has the
+// accuracy of a Householder QR (error ~ cond(A) eps) instead of the
+// cond(A)^2 eps of the normal equations M c = A^T y that Sec. 1.4 writes; the
+// first Cholesky factorisation fails (PROBE_ERR_STATE) only when A is
+// numerically rank deficient.  Gram matrices: P <= 64 -- columns formed on the
+// fly in shared memory, 32 rows at a time (pass 2 applies R1^{-1} to the staged
+// rows in shared memory); P up to 1024 -- [A | y] formed in column-major chunks
+// of about 256 MB, R1^{-1} applied row by row, and a tiled FP64 Gram kernel.
+// A second pass forms ||y - sum_i c_i B_i x|| / ||y||.
 //
 // probe_apply_precond (end of Sec. 1.5): one D2Z transform of the image, one
 // combined multiplier gamma_lam(k) = sum_m c_(lam,m) beta_m(k) per spatial mode,
@@ -29,13 +41,15 @@
 
 namespace probe {
 
-constexpr int kMaxTerms = 64;     // P <= 64: the normal matrix lives in one CTA's shared memory
+constexpr int kMaxTerms = 1024;   // P = nspatial x nangular x nradial
+constexpr int kMaxSmall = 64;     // P <= 64: Gram pairs accumulated in one CTA's registers
 constexpr int kMaxSpatial = 32;
 constexpr int kMaxAngular = 16;
 constexpr int kMaxRadial = 16;
 constexpr int kMaxMult = 32;      // nangular * nradial
 constexpr int kGramRows = 32;     // rows staged per Gram iteration
 constexpr int kGramBlocks = 608;  // 4 CTAs per SM
+constexpr long long kChunkBytes = 256ll << 20;  // large-P path: [A | y] chunk size
 
 struct BasisDev {
     int ndim;
@@ -53,13 +67,15 @@ struct BasisDev {
 struct FitCache {
     std::map<std::tuple<int, int, int, int, int>, cufftHandle> plans;  // (ndim, Nz, Ny, Nx, kind*batch)
     DevBuf xr, Xc, Wc, w, beta, alpha, part, coef, misc;
+    DevBuf gram, L1, L2, chunk;  // CholeskyQR2: Gram matrix, the two Cholesky factors, [A | y] chunk
 };
 
 void fit_cache_destroy(probe_t h) {
     if (!h || !h->fit) return;
     for (auto& kv : h->fit->plans) cufftDestroy(kv.second);
-    DevBuf* bufs[] = {&h->fit->xr, &h->fit->Xc, &h->fit->Wc, &h->fit->w, &h->fit->beta,
-                      &h->fit->alpha, &h->fit->part, &h->fit->coef, &h->fit->misc};
+    DevBuf* bufs[] = {&h->fit->xr, &h->fit->Xc, &h->fit->Wc, &h->fit->w,  &h->fit->beta, &h->fit->alpha,
+                      &h->fit->part, &h->fit->coef, &h->fit->misc, &h->fit->gram, &h->fit->L1, &h->fit->L2,
+                      &h->fit->chunk};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     delete h->fit;
@@ -194,16 +210,20 @@ __device__ __forceinline__ double alpha_at(const double* __restrict__ alpha, int
     return a[iz] * a[nmax + iy] * a[2 * nmax + ix];
 }
 
-// Per-CTA partial sums of the upper triangle of [A y]^T [A y] (pairs (i, k), i <= k <= P).
+// Small-P path (P <= 64).  Per-CTA partial sums of the upper triangle of [A y]^T [A y] (pairs
+// (i, k), i <= k <= P), the columns formed 32 rows at a time in shared memory.  QPASS (pass 2 of
+// CholeskyQR2): the staged A part of each row is first multiplied by R1^{-1} = L1^{-T} in place
+// (eight threads per row, forward substitution), so the sums are those of [Q1 y].
+template <bool QPASS>
 __global__ void __launch_bounds__(256) k_fit_gram(const double* __restrict__ w, const float* __restrict__ y,
                                                   const double* __restrict__ alpha, int nmax, int p, BasisDev B,
-                                                  double* __restrict__ partial) {
+                                                  const double* __restrict__ L1, double* __restrict__ partial) {
     const int P = B.P, PC = P + 1;
     const int npairs = PC * (PC + 1) / 2;
-    __shared__ double cols[kGramRows][kMaxTerms + 1];
+    __shared__ double cols[kGramRows][kMaxSmall + 1];
     __shared__ double wv[kGramRows][kMaxMult];
     __shared__ double av[kGramRows][kMaxSpatial];
-    __shared__ unsigned short pi_[(kMaxTerms + 1) * (kMaxTerms + 2) / 2], pk_[(kMaxTerms + 1) * (kMaxTerms + 2) / 2];
+    __shared__ unsigned short pi_[(kMaxSmall + 1) * (kMaxSmall + 2) / 2], pk_[(kMaxSmall + 1) * (kMaxSmall + 2) / 2];
     for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
         int i = 0, rem = t;
         while (rem >= PC - i) {
@@ -213,12 +233,13 @@ __global__ void __launch_bounds__(256) k_fit_gram(const double* __restrict__ w, 
         pi_[t] = (unsigned short)i;
         pk_[t] = (unsigned short)(i + rem);
     }
-    constexpr int kMaxPairsPerThread = ((kMaxTerms + 1) * (kMaxTerms + 2) / 2 + 255) / 256;
+    constexpr int kMaxPairsPerThread = ((kMaxSmall + 1) * (kMaxSmall + 2) / 2 + 255) / 256;
     double acc[kMaxPairsPerThread];
 #pragma unroll
     for (int s = 0; s < kMaxPairsPerThread; ++s) acc[s] = 0.0;
     const long long rows = (long long)p * B.npts;
     const long long wstride = (long long)p * B.Nreal;  // between multipliers
+    const int tr = threadIdx.x >> 3, l8 = threadIdx.x & 7;  // pass 2: row and lane of the row solve
     __syncthreads();
     for (long long r0 = (long long)blockIdx.x * kGramRows; r0 < rows; r0 += (long long)gridDim.x * kGramRows) {
         // stage multiplier fields, spatial modes and y for kGramRows rows
@@ -252,6 +273,19 @@ __global__ void __launch_bounds__(256) k_fit_gram(const double* __restrict__ w, 
             cols[r][i] = av[r][lam] * wv[r][m];
         }
         __syncthreads();
+        if (QPASS) {  // q_j = (a_j - sum_{i<j} q_i L1_ji) / L1_jj for row tr, lanes l8 split the sum
+            for (int jj = 0; jj < P; ++jj) {
+                const double* Lj = L1 + (long long)jj * P;
+                double sum = 0.0;
+                for (int i = l8; i < jj; i += 8) sum = fma(cols[tr][i], Lj[i], sum);
+                sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+                sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+                sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+                if (l8 == 0) cols[tr][jj] = (cols[tr][jj] - sum) / Lj[jj];
+                __syncwarp();
+            }
+            __syncthreads();
+        }
 #pragma unroll
         for (int s = 0; s < kMaxPairsPerThread; ++s) {
             const int t = threadIdx.x + s * 256;
@@ -272,70 +306,203 @@ __global__ void __launch_bounds__(256) k_fit_gram(const double* __restrict__ w, 
     }
 }
 
-// Single CTA: reduce the partials in a fixed order, Cholesky-factorise M, solve for c.
-// status[0] = 0 ok, 1 = M not numerically positive definite.
-__global__ void __launch_bounds__(256) k_fit_solve(const double* __restrict__ partial, int nblocks, int P,
-                                                   double* __restrict__ coef, int* status) {
-    const int PC = P + 1;
-    const int npairs = PC * (PC + 1) / 2;
-    __shared__ double M[kMaxTerms][kMaxTerms];
-    __shared__ double b[kMaxTerms];
-    __shared__ double z[kMaxTerms];
-    __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
+// Small-P path: the per-CTA pair sums reduced in a fixed order into the dense lower triangle of
+// C (n x n, n = P + 1, row-major): C[k][i] = sum (i <= k).
+__global__ void k_fit_pairs_to_C(const double* __restrict__ partial, int nblocks, int n, double* __restrict__ C) {
+    const int npairs = n * (n + 1) / 2;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npairs; t += gridDim.x * blockDim.x) {
         int i = 0, rem = t;
-        while (rem >= PC - i) {
-            rem -= PC - i;
+        while (rem >= n - i) {
+            rem -= n - i;
             ++i;
         }
         const int k = i + rem;
         double s = 0.0;
         for (int blk = 0; blk < nblocks; ++blk) s += partial[(long long)blk * npairs + t];
-        if (k < P) {
-            M[i][k] = s;
-            M[k][i] = s;
-        } else if (i < P) {
-            b[i] = s;
-        }
+        C[(long long)k * n + i] = s;
     }
-    __syncthreads();
-    double dmax = 0.0;
-    for (int i = 0; i < P; ++i) dmax = fmax(dmax, M[i][i]);
-    // right-looking Cholesky, lower triangle in place
-    for (int k = 0; k < P; ++k) {
-        if (threadIdx.x == 0) {
-            const double d = M[k][k];
-            if (!(d > 1e-13 * dmax)) {
-                bad = 1;
-                M[k][k] = 1.0;
+}
+
+// [A | y] for stacked rows r0 .. r0 + rc - 1 (row = j * npts + pt) as a column-major FP64 block
+// with leading dimension rc: column i < P is (B_i x_j)(pt) = alpha_lam(pt) w_m(j, pt) with
+// i = lam * NM + m, column P is y_j(pt).  Rows past the end are zero (they add nothing).
+__global__ void k_fit_cols(const double* __restrict__ w, const float* __restrict__ y,
+                           const double* __restrict__ alpha, int nmax, int p, BasisDev B, long long r0, int rc,
+                           double* __restrict__ A) {
+    const long long rows = (long long)p * B.npts;
+    const long long wstride = (long long)p * B.Nreal;
+    const long long tot = (long long)rc * (B.P + 1);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int col = (int)(i / rc);
+        const int r = (int)(i - (long long)col * rc);
+        const long long row = r0 + r;
+        double v = 0.0;
+        if (row < rows) {
+            const int j = (int)(row / B.npts);
+            int iz, iy, ix;
+            unravel(row - (long long)j * B.npts, B, iz, iy, ix);
+            if (col < B.P) {
+                const int lam = col / B.NM, m = col - lam * B.NM;
+                v = alpha_at(alpha, nmax, lam, iz, iy, ix) *
+                    w[(long long)m * wstride + (long long)j * B.Nreal + fft_index(B, iz, iy, ix)];
             } else {
-                M[k][k] = sqrt(d);
+                v = (double)y[row];
             }
         }
+        A[i] = v;
+    }
+}
+
+// Gram matrix of a column-major block A (rc rows, n columns, ld rc): tile (ti, tk), ti >= tk, of
+// 64 x 64 entries over the rows of slice blockIdx.y; part[slice][i * n + k] for every (i, k) of
+// the tile (the diagonal tiles hold both triangles).  256 threads, 4 x 4 entries each.
+constexpr int kSyT = 64, kSyR = 32;
+__global__ void __launch_bounds__(256) k_fit_syrk(const double* __restrict__ A, int rc, int n, int rows_per_slice,
+                                                  double* __restrict__ part) {
+    __shared__ double As[kSyR][kSyT + 1], Bs[kSyR][kSyT + 1];
+    int t = blockIdx.x, ti = 0;
+    while (t > ti) {  // lower tiles in row order: (0,0), (1,0), (1,1), (2,0), ...
+        t -= ti + 1;
+        ++ti;
+    }
+    const int tk = t;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int r_beg = blockIdx.y * rows_per_slice, r_end = min(rc, r_beg + rows_per_slice);
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int r0 = r_beg; r0 < r_end; r0 += kSyR) {
+        for (int q = threadIdx.x; q < kSyR * kSyT; q += 256) {
+            const int r = q & (kSyR - 1), c = q / kSyR;
+            const int row = r0 + r;
+            const int ci = ti * kSyT + c, ck = tk * kSyT + c;
+            As[r][c] = (row < r_end && ci < n) ? A[(long long)ci * rc + row] : 0.0;
+            Bs[r][c] = (row < r_end && ck < n) ? A[(long long)ck * rc + row] : 0.0;
+        }
         __syncthreads();
-        for (int i = k + 1 + threadIdx.x; i < P; i += blockDim.x) M[i][k] /= M[k][k];
-        __syncthreads();
-        const int m = P - k - 1;
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            const int i = k + 1 + t / m, j = k + 1 + t % m;
-            if (j <= i) M[i][j] -= M[i][k] * M[j][k];
+#pragma unroll 4
+        for (int r = 0; r < kSyR; ++r) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[r][ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[r][tx * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
         }
         __syncthreads();
     }
+    double* out = part + (long long)blockIdx.y * n * n;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = ti * kSyT + ty * 4 + a;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int k = tk * kSyT + tx * 4 + b;
+            if (i < n && k < n) out[(long long)i * n + k] = acc[a][b];
+        }
+    }
+}
+
+// C[e] (+)= sum over slices of part[s][e] for the lower triangle, in slice order.
+__global__ void k_fit_reduce(const double* __restrict__ part, int nslices, int n, int accumulate,
+                             double* __restrict__ C) {
+    const long long tot = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), k = (int)(e - (long long)i * n);
+        if (k > i) continue;
+        double s = accumulate ? C[e] : 0.0;
+        for (int q = 0; q < nslices; ++q) s += part[(long long)q * tot + e];
+        C[e] = s;
+    }
+}
+
+// Largest diagonal entry of the leading P x P block of S (ld = ld) -> *dmax.
+__global__ void k_fit_dmax(const double* __restrict__ S, int ld, int P, double* dmax) {
+    double m = 0.0;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) m = fmax(m, S[(long long)i * ld + i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 0; i < P; ++i) {  // L z = b
-            double s = b[i];
-            for (int j = 0; j < i; ++j) s -= M[i][j] * z[j];
-            z[i] = s / M[i][i];
-        }
-        for (int i = P - 1; i >= 0; --i) {  // L^T c = z
-            double s = z[i];
-            for (int j = i + 1; j < P; ++j) s -= M[j][i] * coef[j];
-            coef[i] = s / M[i][i];
-        }
-        status[0] = bad;
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        *dmax = m;
     }
+}
+
+// Step k of the right-looking Cholesky factorisation S = L L^T of the leading P x P block of S
+// (lower triangle, ld = ld): CTA 0 writes column k of L (ld P); every CTA applies the rank-one
+// update S_ij -= l_ik l_jk to its share of k < j <= i < P.  Column k of S is only read.  A pivot
+// below 1e-13 of the largest diagonal entry marks S as not numerically positive definite.
+__global__ void k_fit_chol_step(double* __restrict__ S, int ld, int P, int k, const double* __restrict__ dmax,
+                                double* __restrict__ L, int* status) {
+    const double d = S[(long long)k * ld + k];
+    const bool bad = !(d > 1e-13 * (*dmax));
+    const double lkk = bad ? 1.0 : sqrt(d);
+    const double inv = 1.0 / lkk;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) {
+            L[(long long)k * P + k] = lkk;
+            if (bad) *status = 1;
+        }
+        for (int i = k + 1 + threadIdx.x; i < P; i += blockDim.x) L[(long long)i * P + k] = S[(long long)i * ld + k] * inv;
+    }
+    const int m = P - k - 1;
+    const long long tot = (long long)m * m;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = k + 1 + (int)(t / m), j = k + 1 + (int)(t % m);
+        if (j > i) continue;
+        S[(long long)i * ld + j] -= (S[(long long)i * ld + k] * inv) * (S[(long long)j * ld + k] * inv);
+    }
+}
+
+// Rows of a column-major block A (rc rows, first P columns) times R^{-1} = L^{-T}, in place:
+// q_j = (a_j - sum_{i<j} q_i L_ji) / L_jj, one thread per row.
+__global__ void k_fit_trsm_rows(double* __restrict__ A, int rc, int P, const double* __restrict__ L) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rc) return;
+    for (int j = 0; j < P; ++j) {
+        const double* Lj = L + (long long)j * P;
+        double s = A[(long long)j * rc + r];
+        for (int i = 0; i < j; ++i) s = fma(-A[(long long)i * rc + r], Lj[i], s);
+        A[(long long)j * rc + r] = s / Lj[j];
+    }
+}
+
+// One CTA: x = L^{-1} b (trans = 0) or x = L^{-T} b (trans = 1), L lower with ld P; x may alias b.
+__global__ void __launch_bounds__(256) k_fit_trsv(const double* __restrict__ L, int P, int trans,
+                                                  const double* b, double* x) {
+    __shared__ double xs[kMaxTerms];
+    __shared__ double red[8];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) xs[i] = b[i];
+    __syncthreads();
+    for (int s = 0; s < P; ++s) {
+        const int i = trans ? P - 1 - s : s;
+        double part = 0.0;
+        if (!trans) {
+            for (int j = threadIdx.x; j < i; j += blockDim.x) part = fma(L[(long long)i * P + j], xs[j], part);
+        } else {
+            for (int j = i + 1 + threadIdx.x; j < P; j += blockDim.x) part = fma(L[(long long)j * P + i], xs[j], part);
+        }
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            xs[i] = (xs[i] - t) / L[(long long)i * P + i];
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < P; i += blockDim.x) x[i] = xs[i];
 }
 
 // Per-CTA sums of (y - sum_i c_i col_i)^2 and y^2.
@@ -447,7 +614,7 @@ probe_status make_basis(probe_t h, const probe_basis* bs, BasisDev& B) {
     B.NM = bs->nangular * bs->nradial;
     B.P = B.nspatial * B.NM;
     if (B.NM > kMaxMult) return fail(h, PROBE_ERR_ARG, "nangular * nradial must be <= 32");
-    if (B.P > kMaxTerms) return fail(h, PROBE_ERR_ARG, "the number of terms P must be <= 64");
+    if (B.P > kMaxTerms) return fail(h, PROBE_ERR_ARG, "the number of terms P must be <= 1024");
     for (int l = 0; l < B.nspatial; ++l)
         for (int a = 0; a < bs->ndim; ++a) B.spatial[l][a] = bs->spatial[l * bs->ndim + a];
     for (int a = 0; a < B.nangular; ++a) {
@@ -516,6 +683,85 @@ probe_status tables(probe_t h, const BasisDev& B, cudaStream_t st, double** beta
     return PROBE_OK;
 }
 
+// Gram matrix [A | y]^T [A | y] (pass 1) or [Q1 | y]^T [Q1 | y] with Q1 = A R1^{-1} (pass 2, L1 =
+// R1^T given) into the dense lower triangle of C (n x n, n = P + 1).
+probe_status fit_gram(probe_t h, const BasisDev& B, const double* w, const float* yd, const double* alpha, int nmax,
+                      int p, const double* L1, double* C, cudaStream_t st) {
+    FitCache& c = *h->fit;
+    const int P = B.P, n = P + 1;
+    const long long rows = (long long)p * B.npts;
+    if (P <= kMaxSmall) {
+        const int npairs = n * (n + 1) / 2;
+        PROBE_TRY(ensure_buf(h, c.part, (size_t)kGramBlocks * npairs * 8));
+        if (L1)
+            k_fit_gram<true><<<kGramBlocks, 256, 0, st>>>(w, yd, alpha, nmax, p, B, L1, (double*)c.part.p);
+        else
+            k_fit_gram<false><<<kGramBlocks, 256, 0, st>>>(w, yd, alpha, nmax, p, B, nullptr, (double*)c.part.p);
+        k_fit_pairs_to_C<<<grid_of(npairs), 256, 0, st>>>((const double*)c.part.p, kGramBlocks, n, C);
+        PROBE_CK(h, cudaGetLastError());
+        return PROBE_OK;
+    }
+    long long rcl = std::max<long long>(1024, kChunkBytes / (8ll * n));
+    rcl = std::min(rcl, (rows + 31) / 32 * 32);
+    const int rc = (int)((rcl + 31) / 32 * 32);
+    const int T = (n + kSyT - 1) / kSyT, tiles = T * (T + 1) / 2;
+    const int nslices = std::max(1, std::min(kGramBlocks / tiles, (rc + 255) / 256));
+    const int rps = ((rc + nslices - 1) / nslices + kSyR - 1) / kSyR * kSyR;
+    PROBE_TRY(ensure_buf(h, c.chunk, (size_t)rc * n * 8));
+    PROBE_TRY(ensure_buf(h, c.part, (size_t)nslices * n * n * 8));
+    double* A = (double*)c.chunk.p;
+    for (long long r0 = 0; r0 < rows; r0 += rc) {
+        k_fit_cols<<<grid_of((long long)rc * n), 256, 0, st>>>(w, yd, alpha, nmax, p, B, r0, rc, A);
+        if (L1) k_fit_trsm_rows<<<(rc + 127) / 128, 128, 0, st>>>(A, rc, P, L1);
+        k_fit_syrk<<<dim3(tiles, nslices), 256, 0, st>>>(A, rc, n, rps, (double*)c.part.p);
+        k_fit_reduce<<<grid_of((long long)n * n), 256, 0, st>>>((const double*)c.part.p, nslices, n, r0 > 0 ? 1 : 0,
+                                                               C);
+        PROBE_CK(h, cudaGetLastError());
+    }
+    return PROBE_OK;
+}
+
+// Cholesky factor L (P x P, lower, ld P) of the leading block of C (ld n), destroying that block.
+probe_status fit_cholesky(probe_t h, double* C, int n, int P, double* L, double* dmax, int* status,
+                          cudaStream_t st) {
+    PROBE_CK(h, cudaMemsetAsync(L, 0, (size_t)P * P * 8, st));
+    k_fit_dmax<<<1, 256, 0, st>>>(C, n, P, dmax);
+    for (int k = 0; k < P; ++k) {
+        const long long m = (long long)(P - k - 1) * (P - k - 1);
+        k_fit_chol_step<<<(int)std::max<long long>(1, std::min<long long>((m + 255) / 256, 1024)), 256, 0, st>>>(
+            C, n, P, k, dmax, L, status);
+    }
+    PROBE_CK(h, cudaGetLastError());
+    return PROBE_OK;
+}
+
+// CholeskyQR2 least squares of the fit: coefficients into coef (device, P); status[0] = 1 when
+// A^T A (or Q1^T Q1) is not numerically positive definite.
+probe_status fit_solve_cqr2(probe_t h, const BasisDev& B, const double* w, const float* yd, const double* alpha,
+                            int nmax, int p, double* coef, int* status, cudaStream_t st) {
+    FitCache& c = *h->fit;
+    const int P = B.P, n = P + 1;
+    PROBE_TRY(ensure_buf(h, c.gram, (size_t)n * n * 8));
+    PROBE_TRY(ensure_buf(h, c.L1, (size_t)P * P * 8));
+    PROBE_TRY(ensure_buf(h, c.L2, (size_t)P * P * 8));
+    double* C = (double*)c.gram.p;
+    double* L1 = (double*)c.L1.p;
+    double* L2 = (double*)c.L2.p;
+    double* dmax = (double*)c.misc.p + 2;
+    double* v = coef + P;  // scratch of P doubles after the coefficients
+    PROBE_CK(h, cudaMemsetAsync(status, 0, sizeof(int), st));
+    PROBE_TRY(fit_gram(h, B, w, yd, alpha, nmax, p, nullptr, C, st));   // [A y]^T [A y]
+    PROBE_TRY(fit_cholesky(h, C, n, P, L1, dmax, status, st));         // R1 = L1^T
+    PROBE_TRY(fit_gram(h, B, w, yd, alpha, nmax, p, L1, C, st));        // [Q1 y]^T [Q1 y]
+    PROBE_TRY(fit_cholesky(h, C, n, P, L2, dmax, status, st));         // R2 = L2^T
+    const double* z = C + (long long)P * n;                             // Q1^T y (row P of C)
+    k_fit_trsv<<<1, 256, 0, st>>>(L2, P, 0, z, v);                      // R2^{-T} z
+    k_fit_trsv<<<1, 256, 0, st>>>(L2, P, 1, v, v);                      // R2^{-1} R2^{-T} z
+    k_fit_trsv<<<1, 256, 0, st>>>(L1, P, 1, v, coef);                   // c = R1^{-1} (...)
+    PROBE_CK(h, cudaGetLastError());
+    return PROBE_OK;
+}
+
 }  // namespace
 }  // namespace probe
 
@@ -541,8 +787,7 @@ extern "C" probe_status probe_fit(probe_t h, const probe_basis* basis, const flo
         if ((s = ensure_buf(h, c.Xc, (size_t)p * B.Ncplx * 16)) != PROBE_OK) break;
         if ((s = ensure_buf(h, c.Wc, (size_t)p * B.Ncplx * 16)) != PROBE_OK) break;
         if ((s = ensure_buf(h, c.w, (size_t)B.NM * p * B.Nreal * 8)) != PROBE_OK) break;
-        if ((s = ensure_buf(h, c.part, (size_t)kGramBlocks * (kMaxTerms + 1) * (kMaxTerms + 2) / 2 * 8)) != PROBE_OK) break;
-        if ((s = ensure_buf(h, c.coef, (size_t)(kMaxTerms + 8) * 8)) != PROBE_OK) break;
+        if ((s = ensure_buf(h, c.coef, (size_t)(2 * B.P + 8) * 8)) != PROBE_OK) break;
         if ((s = ensure_buf(h, c.misc, 64)) != PROBE_OK) break;
         double *beta, *alpha;
         int nmax;
@@ -562,10 +807,10 @@ extern "C" probe_status probe_fit(probe_t h, const probe_basis* basis, const flo
                           "Z2D");
         }
         if (s != PROBE_OK) break;
-        k_fit_gram<<<kGramBlocks, 256, 0, st>>>((const double*)c.w.p, yd, alpha, nmax, p, B, (double*)c.part.p);
         int* status = (int*)c.misc.p;
         double* coef = (double*)c.coef.p;
-        k_fit_solve<<<1, 256, 0, st>>>((const double*)c.part.p, kGramBlocks, B.P, coef, status);
+        if ((s = fit_solve_cqr2(h, B, (const double*)c.w.p, yd, alpha, nmax, p, coef, status, st)) != PROBE_OK) break;
+        if ((s = ensure_buf(h, c.part, (size_t)kGramBlocks * 2 * 8)) != PROBE_OK) break;
         k_fit_resid<<<kGramBlocks, 256, 0, st>>>((const double*)c.w.p, yd, alpha, nmax, p, B, coef, (double*)c.part.p);
         k_fit_resid_final<<<1, 32, 0, st>>>((const double*)c.part.p, kGramBlocks, (double*)c.misc.p + 1);
         if ((e = cudaGetLastError()) != cudaSuccess) { s = cuda_fail(h, e, "fit kernels"); break; }
@@ -580,7 +825,7 @@ extern "C" probe_status probe_fit(probe_t h, const probe_basis* basis, const flo
             break;
         }
         if (resid_rel) *resid_rel = res_h;
-        if (stat_h) s = fail(h, PROBE_ERR_STATE, "normal matrix M is not numerically positive definite");
+        if (stat_h) s = fail(h, PROBE_ERR_STATE, "the fit columns B_i x_j are numerically rank deficient");
     } while (0);
     cudaStreamSynchronize(st);
     if (ystage.p) cudaFree(ystage.p);
@@ -612,7 +857,7 @@ extern "C" probe_status probe_apply_precond(probe_t h, const probe_basis* basis,
         if ((s = ensure_buf(h, c.Xc, (size_t)B.Ncplx * 16)) != PROBE_OK) break;
         if ((s = ensure_buf(h, c.Wc, (size_t)B.nspatial * B.Ncplx * 16)) != PROBE_OK) break;
         if ((s = ensure_buf(h, c.w, (size_t)B.nspatial * B.Nreal * 8)) != PROBE_OK) break;
-        if ((s = ensure_buf(h, c.coef, (size_t)(kMaxTerms + 8) * 8)) != PROBE_OK) break;
+        if ((s = ensure_buf(h, c.coef, (size_t)(2 * B.P + 8) * 8)) != PROBE_OK) break;
         if ((s = ensure_buf(h, c.part, (size_t)B.nspatial * B.Ncplx * 8)) != PROBE_OK) break;
         double *beta, *alpha;
         int nmax;

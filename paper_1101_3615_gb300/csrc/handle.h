@@ -33,6 +33,7 @@ struct Workspace {
     float* absmax = nullptr;  // [W*2]
     float* dtt = nullptr;     // [W][K][F]
     float* img = nullptr;     // [groups][nb][F]
+    float* seg = nullptr;     // 3D one-field adjoint with Kahan: plain FP32 image of one checkpoint segment
     float* comp = nullptr;
     float* s_tmp = nullptr;   // [F]
     int* src_wave = nullptr;  // [W][2] padded sources of the wave
@@ -107,6 +108,7 @@ struct probe_s {
     int opt_check_finite = 1, opt_shot_wave = 0, opt_shot_group = 0, opt_use_graph = 0;
     int opt_timing = 0, opt_tile_z = 0, opt_pipeline = 2, opt_dtt_history = 0;
     int opt_autotune = 1;        // time the kernel variants on first use of a shape
+    int opt_cluster3d = 0;       // 3D cluster kernels: bit 0 fused forward, bit 1 shot-clustered adjoint
     int pipe_adj = 2;            // adjoint kernel variant (the forward uses opt_pipeline)
     int user_fixed = 0;          // the caller chose pipeline / shot group: no autotuning
     std::vector<probe::TunedEntry> tuned;  // autotuner results by workload key

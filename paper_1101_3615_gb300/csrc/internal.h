@@ -131,19 +131,33 @@ struct alignas(128) ModelStep3D {
     float* data;
     const float* rdata;
     long long dss, dts;
-    float* img;                // adjoint: [W][nb][F]
+    float* img;                // adjoint: [W][nb][F] (one-field kernels) or [W / G][nb][F] (shot clusters)
     float* comp;
+    int seg_first;             // one-field adjoint into a segment image: first step of the segment (img = t)
+    // shot-cluster adjoint: receiver injection R^T r^n prebuilt per checkpoint segment for the
+    // planes that hold receivers ("bands"), inj[slot][shot][trial][band][Ny][P], slot = n_hi - n
+    const int* rrow;           // [Nz] band of a plane, -1 without receivers
+    const float* inj;
+    int inj_slot;
+    long long inj_block;       // floats per (slot, shot, trial) block = nband * Ny * P
 };
 
 struct StepParams3D {
     int n, nt;
     int* err;
     ModelStep3D m;
+    ModelStep3D m2;  // cluster kernels: the Born fields of the fused forward step
 };
 
 // pipelined: the producer-warp variant for the forward modes (the adjoint always uses k_step3d)
 cudaError_t launch_step3d(int mode, bool kahan, bool pipelined, const StepParams3D& p, cudaStream_t st);
 size_t step3d_smem_bytes();
+// Fused incident + Born step on clusters of 1 + nb CTAs (m: incident, m2: Born, nb = m2.nfield <= 7).
+cudaError_t launch_fwd3d_cluster(const StepParams3D& p, cudaStream_t st);
+size_t fwd3d_cluster_smem_bytes();
+// Adjoint + imaging on clusters of G shots (G = 1, 2, 4, 8; m.nshots % G == 0): one image per
+// (shot group, trial), img [nshots / G][nb][F].
+cudaError_t launch_adj3d_cluster(int G, bool kahan, const StepParams3D& p, cudaStream_t st);
 
 // Launchers (stencil2d.cu).  `zblocks` = grid.z extent: shots (forward) or shot
 // groups (adjoint) summed over the models of the launch.
@@ -190,6 +204,9 @@ cudaError_t launch_encode_ckpt(const float* state, int nplanes, long long F, int
 cudaError_t launch_decode_ckpt(const void* src, const float* scales, int nplanes, long long F,
                                int pc, int dtype, float* state, cudaStream_t st);
 cudaError_t launch_scale_copy(const float* src, float* dst, long long n, float a, cudaStream_t st);
+// img, comp (+)= seg with Kahan compensation (n floats): the end of a checkpoint segment of the 3D
+// adjoint, whose steps summed their imaging terms into the plain FP32 segment image seg.
+cudaError_t launch_kahan_fold(float* img, float* comp, const float* seg, long long n, cudaStream_t st);
 cudaError_t launch_diag_wait(int* err, unsigned long long limit_ns, cudaStream_t st);
 
 }  // namespace probe

@@ -141,13 +141,17 @@ std::atomic<long long> g_generation{0};
 
 void free_ws(Workspace& w) {
     void* ptrs[] = {w.u, w.f, w.dm, w.data, w.ckpt, w.scales, w.absmax, w.dtt, w.img, w.comp, w.s_tmp,
-                    w.src_wave, w.inj};
+                    w.src_wave, w.inj, w.seg};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Workspace();
     w.generation = ++g_generation;
 }
 
+
+// Floats of one (slot, shot, trial) block of the adjoint injection buffer: the grid rows (2D) or
+// planes (3D) that hold receivers.
+long long inj_block(probe_t h) { return (long long)h->nband * (h->ndim == 3 ? (long long)h->Ny * h->P : h->P); }
 
 // Bytes per resident shot and fixed bytes of a job with nb trials.
 bool use_history(probe_t h, int with_ckpt) { return with_ckpt && h->opt_dtt_history && h->ndim == 2; }
@@ -160,7 +164,11 @@ void ws_bytes(probe_t h, int nb, int with_ckpt, int with_data, double* per_shot,
     else if (with_ckpt)
         ps += (double)h->nck * ckpt_bytes_per_shot(h->snap, h->F) + (double)h->K * F4 + 16.0 * h->nck;
     if (with_data) ps += (double)nb * h->nt * h->nr * 4.0;
-    if (h->ndim == 3 && with_ckpt) ps += 2.0 * nb * F4;  // per-shot images + compensation
+    if (h->ndim == 3 && with_ckpt) {
+        ps += 2.0 * nb * F4;  // per-shot images + compensation
+        if (h->opt_cluster3d & 2) ps += (double)h->K * nb * inj_block(h) * 4.0;  // injection of one segment
+        else if (h->kahan) ps += (double)nb * F4;                                 // segment images
+    }
     *per_shot = ps;
     *fixed = nb * F4 + 2.0 * F4 * nb + F4;  // dm, one image group, s_tmp
 }
@@ -172,12 +180,23 @@ int plan_wave(probe_t h, int nb, int with_ckpt, int with_data) {
     size_t freeb = 0, totb = 0;
     cudaMemGetInfo(&freeb, &totb);
     const double budget = 0.80 * (double)freeb + (double)h->ws.bytes;
-    int W = (int)std::floor((budget - fx) / ps);
-    return std::max(1, std::min(W, h->ns));
+    int W = std::max(1, std::min((int)std::floor((budget - fx) / ps), h->ns));
+    // equal waves: the fewest waves that fit, with the shots spread evenly over them (so that the
+    // last wave is not a remainder of one or two shots)
+    const int nwaves = (h->ns + W - 1) / W;
+    return (h->ns + nwaves - 1) / nwaves;
 }
 
 int pick_group(probe_t h, int W) {
-    if (h->ndim == 3) return 1;  // 3D kernels accumulate one image per shot and trial
+    if (h->ndim == 3) {
+        // one-field kernels: one image per shot and trial; cluster kernels: clusters of g shots,
+        // g in {1, 2, 4, 8} dividing every wave (the full waves and the last one)
+        if (!(h->opt_cluster3d & 2)) return 1;
+        const int last = (h->ns % W) ? h->ns % W : W;
+        int g = h->opt_shot_group > 0 ? std::min(h->opt_shot_group, 8) : 4;
+        while (g > 1 && ((g & (g - 1)) || W % g || last % g)) --g;
+        return std::max(g, 1);
+    }
     if (h->opt_shot_group > 0) return std::min(h->opt_shot_group, W);
     return std::min(4, W);
 }
@@ -236,10 +255,14 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     }
     TRY(alloc((void**)&w.img, (size_t)G * std::max(nb, 1) * F * 4));
     TRY(alloc((void**)&w.comp, (size_t)G * std::max(nb, 1) * F * 4));
+    if (h->ndim == 3 && with_ckpt && h->kahan && !(h->opt_cluster3d & 2)) {
+        TRY(alloc((void**)&w.seg, (size_t)W * std::max(nb, 1) * F * 4));
+        CK(h, cudaMemset(w.seg, 0, (size_t)W * std::max(nb, 1) * F * 4));  // pitch columns stay zero
+    }
     TRY(alloc((void**)&w.s_tmp, (size_t)F * 4));
     TRY(alloc((void**)&w.src_wave, (size_t)W * 3 * 4));
-    if (with_ckpt && h->ndim == 2 && h->nband > 0)  // one segment of adjoint injection
-        TRY(alloc((void**)&w.inj, (size_t)h->K * W * std::max(nb, 1) * h->nband * h->P * 4));
+    if (with_ckpt && h->nband > 0 && (h->ndim == 2 || (h->opt_cluster3d & 2)))  // one segment of adjoint injection
+        TRY(alloc((void**)&w.inj, (size_t)h->K * W * std::max(nb, 1) * inj_block(h) * 4));
     // field planes must read as zero outside what the kernels write
     CK(h, cudaMemset(w.u, 0, (size_t)W * 2 * F * 4));
     CK(h, cudaMemset(w.f, 0, (size_t)W * std::max(nb, 1) * 2 * F * 4));
@@ -280,23 +303,29 @@ probe_status upload_csr(probe_t h, const std::vector<int>& key, int nkeys, int**
 
 // 2D adjoint injection layout: the grid rows that hold receivers (bands) and the distinct
 // receiver cells with their receivers in receiver order (so sums are formed in a fixed order).
+// 3D: the same with the z planes that hold receivers as bands, position band * Ny * P + y * P + x.
 probe_status build_bands(probe_t h) {
+    const int d = h->ndim;
     std::vector<int> rrow(h->Nz, -1);
     int nband = 0;
     for (int r = 0; r < h->nr; ++r) {
-        const int z = h->rec_pad[2 * r];
+        const int z = h->rec_pad[d * r];
         if (rrow[z] < 0) rrow[z] = 0;
     }
     for (int z = 0; z < h->Nz; ++z)
         if (rrow[z] == 0) rrow[z] = nband++;
-    std::map<std::pair<int, int>, std::vector<int>> cells;  // (band, x) -> receivers
-    for (int r = 0; r < h->nr; ++r)
-        cells[{rrow[h->rec_pad[2 * r]], h->rec_pad[2 * r + 1]}].push_back(r);
+    const long long plane = (d == 3) ? (long long)h->Ny * h->P : h->P;
+    std::map<std::pair<int, long long>, std::vector<int>> cells;  // (band, cell in the band) -> receivers
+    for (int r = 0; r < h->nr; ++r) {
+        const long long in_band = (d == 3) ? (long long)h->rec_pad[3 * r + 1] * h->P + h->rec_pad[3 * r + 2]
+                                           : h->rec_pad[2 * r + 1];
+        cells[{rrow[h->rec_pad[d * r]], in_band}].push_back(r);
+    }
     std::vector<int> ptr(1, 0), rec, pos;
     for (const auto& kv : cells) {
         for (int r : kv.second) rec.push_back(r);
         ptr.push_back((int)rec.size());
-        pos.push_back(kv.first.first * h->P + kv.first.second);
+        pos.push_back((int)(kv.first.first * plane + kv.first.second));
     }
     auto upload = [&](int** dst, const std::vector<int>& v) -> probe_status {
         CK(h, cudaMalloc(dst, std::max<size_t>(v.size(), 1) * 4));
@@ -337,7 +366,7 @@ probe_status build_rec_tiles(probe_t h) {
         }
     }
     TRY(upload_csr(h, key, nkeys, &h->d_rec_tile_ptr, &h->d_rec_tile_idx));
-    if (h->ndim == 2 && !h->d_rrow) TRY(build_bands(h));
+    if (!h->d_rrow) TRY(build_bands(h));
     if (h->ndim == 2) {
         for (int R = 1; R <= 2; ++R) {  // tiles of the pipelined kernels (64 x 16R)
             const int tz = (h->Nz + 16 * R - 1) / (16 * R);
@@ -618,7 +647,7 @@ probe_status build_injection(Sweep& sw, int n_hi, int n_lo) {
         probe_t h = jb.h;
         Workspace& w = h->ws;
         if (!w.inj || h->nband == 0) continue;
-        const long long block = (long long)h->nband * h->P;
+        const long long block = inj_block(h);
         const int nb = std::max(jb.nb, 1);
         CK(h, cudaMemsetAsync(w.inj, 0, (size_t)(n_hi - n_lo + 1) * jb.W * nb * block * 4, sw.st));
         cudaError_t e = launch_build_injection(jb.rdata, jb.dss, jb.dts, h->nr, n_hi, n_hi - n_lo + 1, jb.W, nb,
@@ -774,6 +803,17 @@ probe_status run_forward3d(const Job& jb, FwdKind kind, bool ckpt, cudaStream_t 
         pb.m.Din_shot_stride = dtt_stride3(h);
     }
     const int imode = (kind == FWD_INCIDENT_SAMPLE) ? STEP3_INC_SAMPLE : STEP3_INC;
+    // fused incident + Born step on thread-block clusters (Dtt u0 exchanged in shared memory)
+    const bool fused = born && (h->opt_cluster3d & 1) && jb.nb + 1 <= 8;
+    StepParams3D pf;
+    if (fused) {
+        pf.nt = h->nt;
+        pf.err = h->d_err;
+        pf.m = pi.m;
+        pf.m.Dout = nullptr;
+        pf.m2 = pb.m;
+        pf.m2.Din = nullptr;
+    }
     for (int n = 0; n < h->nt - 1; ++n) {
         if (ckpt && n % h->K == 0) {
             const int k = n / h->K;
@@ -783,6 +823,13 @@ probe_status run_forward3d(const Job& jb, FwdKind kind, bool ckpt, cudaStream_t 
                                                h->snap, w.absmax, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint store");
             c.other += (h->snap == PROBE_SNAP_FP32) ? 0 : 2;
+        }
+        if (fused) {
+            pf.n = n;
+            cudaError_t e = launch_fwd3d_cluster(pf, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "fused forward step launch");
+            c.fwd++;
+            continue;
         }
         TRY(launch3(h, imode, pi, n, st, "incident step launch"));
         c.fwd++;
@@ -822,6 +869,16 @@ probe_status run_adjoint3d(const Job& jb, cudaStream_t st, Count3& c) {
     pa.m.nfield = jb.nb;
     pa.m.nvol_shot = 2 * jb.nb;
     pa.m.Din_shot_stride = dtt_stride3(h);
+    // shot-cluster adjoint: images of shot groups summed in shared memory, receiver injection
+    // prebuilt per segment for the planes that hold receivers
+    const bool clustered = (h->opt_cluster3d & 2) != 0;
+    const int G = pick_group(h, h->ws.W);
+    const long long block = inj_block(h);
+    if (clustered) {
+        pa.m.rrow = (h->nband > 0) ? h->d_rrow : nullptr;
+        pa.m.inj = w.inj;
+        pa.m.inj_block = block;
+    }
     int ev = 2;
     for (int k = h->nck - 1; k >= 0; --k) {
         const int k0 = k * h->K;
@@ -840,10 +897,36 @@ probe_status run_adjoint3d(const Job& jb, cudaStream_t st, Count3& c) {
             c.rec++;
         }
         record(h, ev++, st);
+        if (clustered && h->nband > 0) {  // R^T r^n of levels k1 .. k0 + 1, slot k1 - n
+            CK(h, cudaMemsetAsync(w.inj, 0, (size_t)(k1 - k0) * jb.W * jb.nb * block * 4, st));
+            cudaError_t e = launch_build_injection(jb.rdata, jb.dss, jb.dts, h->nr, k1, k1 - k0, jb.W, jb.nb, h->nuc,
+                                                   h->d_uc_ptr, h->d_uc_rec, h->d_uc_pos, w.inj, block, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "receiver injection");
+            c.other++;
+        }
         for (int n = k1; n >= k0 + 1; --n) {
             pa.m.Din = w.dtt + (long long)(n - 1 - k0) * h->F;
-            TRY(launch3(h, STEP3_ADJ, pa, n, st, "adjoint step launch"));
+            if (clustered) {
+                pa.n = n;
+                pa.m.inj_slot = k1 - n;
+                cudaError_t e = launch_adj3d_cluster(G, h->kahan != 0, pa, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step launch");
+            } else if (w.seg) {
+                // two-level imaging sum: plain FP32 within the segment, Kahan across segments
+                pa.n = n;
+                pa.m.img = w.seg;
+                pa.m.seg_first = (n == k1) ? 1 : 0;
+                cudaError_t e = launch_step3d(STEP3_ADJ, false, h->opt_pipeline != 0, pa, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step launch");
+            } else {
+                TRY(launch3(h, STEP3_ADJ, pa, n, st, "adjoint step launch"));
+            }
             c.adj++;
+        }
+        if (w.seg) {
+            cudaError_t e = launch_kahan_fold(w.img, w.comp, w.seg, (long long)jb.W * jb.nb * h->F, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "segment image fold");
+            c.other++;
         }
     }
     record(h, ev++, st);
@@ -1182,6 +1265,11 @@ extern "C" probe_status probe_set_option(probe_t h, int key, long long v) {
             h->user_fixed = 1;
             return PROBE_OK;
         case PROBE_OPT_USE_GRAPH: h->opt_use_graph = v ? 1 : 0; return PROBE_OK;
+        case PROBE_OPT_CLUSTER3D:
+            if (v < 0 || v > 3) return fail(h, PROBE_ERR_ARG, "cluster3d must be 0..3");
+            h->opt_cluster3d = (int)v;
+            free_ws(h->ws);  // the adjoint's image and injection buffers depend on it
+            return PROBE_OK;
         case PROBE_OPT_TIMING:
             if (v < 0 || v > 2) return fail(h, PROBE_ERR_ARG, "timing must be 0, 1 or 2");
             h->opt_timing = (int)v;
@@ -1542,10 +1630,13 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
         const int nfields = (kind == FWD_BORN) ? 1 + nbw : 1;
         h->stats.cell_updates_forward += cells * steps * Wv * nfields;
         // algorithmic bytes: incident 16 B (u^n, u^{n-1}, s, write), Born +16 B per trial
-        // (du^n, du^{n-1}, dm, write); +4 B Dtt write in the recompute
+        // (du^n, du^{n-1}, dm, write); +4 B Dtt write in the recompute.  The 3D one-field kernels
+        // (no cluster fusion) also write Dtt u^n (4 B) and read it and s once per trial (8 B).
         const bool hist = w.history != 0;
+        const bool split3 = h->ndim == 3 && kind == FWD_BORN && !((h->opt_cluster3d & 1) && nbw + 1 <= 8);
         h->stats.bytes_forward += cells * steps * Wv *
-                                  (16.0 + (kind == FWD_BORN ? 16.0 * nbw : 0.0) + (hist ? 4.0 : 0.0));
+                                  (16.0 + (kind == FWD_BORN ? 16.0 * nbw : 0.0) + (hist ? 4.0 : 0.0) +
+                                   (split3 ? 4.0 + 8.0 * nbw : 0.0));
         if (need_ckpt) {
             if (!hist) {
                 h->stats.cell_updates_recompute += cells * steps * Wv;
@@ -1554,7 +1645,10 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
             h->stats.cell_updates_adjoint += cells * steps * Wv * nbw;
             // adjoint: per (shot, trial) mu^{n+1}, mu^{n+2}, write mu^n = 12 B; per shot Dtt 4 B;
             // s 4 B and image traffic per (group, trial) amortised over the group
-            const double img_b = (h->kahan ? 16.0 : 8.0);
+            // (3D one-field adjoint with Kahan: 8 B segment-image read-modify-write per step, the
+            //  Kahan fold of 20 B per cell once per segment)
+            const bool seg3 = w.seg != nullptr;
+            const double img_b = seg3 ? 8.0 + 20.0 / h->K : (h->kahan ? 16.0 : 8.0);
             h->stats.bytes_adjoint += cells * steps * (12.0 * Wv * nbw + 4.0 * Wv +
                                                        (double)jb.groups * (4.0 + img_b * nbw));
         }

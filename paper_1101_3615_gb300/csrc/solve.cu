@@ -76,6 +76,14 @@ __global__ void k_direction(float* p, const float* z, float beta, long long n) {
         p[i] = __fmaf_rn(beta, p[i], z[i]);
 }
 
+// y = x / sqrt(*sumsq) (y = 0 when the norm is zero); the norm is read on the device.
+__global__ void k_scale_by_norm(float* y, const float* x, const double* sumsq, long long n) {
+    const double s = *sumsq;
+    const float inv = (s > 0.0) ? (float)(1.0 / sqrt(s)) : 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __fmul_rn(x[i], inv);
+}
+
 // r = rhs - Hx.
 __global__ void k_residual(float* r, const float* rhs, const float* Hx, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -213,5 +221,55 @@ extern "C" probe_status probe_solve(probe_t h, int method, int iters, const prob
         cudaStreamSynchronize(st);
     }
     b.release();
+    return s;
+}
+
+// Krylov trial functions of the Kn preconditioners (Sec. 2): y_1 = rhs / ||rhs||, x_j = H y_j,
+// y_{j+1} = x_j / ||x_j||.  The norms are FP64 sums on the device; nothing is read back between
+// the H applications.
+extern "C" probe_status probe_krylov_trials(probe_t h, const float* rhs, int n, float* y, float* Hy,
+                                            probe_stream_t stream) {
+    if (!h) return PROBE_ERR_ARG;
+    if (n < 1) return fail(h, PROBE_ERR_ARG, "n must be >= 1");
+    if (!rhs || !y || !Hy) return fail(h, PROBE_ERR_ARG, "NULL array");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long m = h->nmodel;
+    const bool dev_y = is_device_ptr(y), dev_x = is_device_ptr(Hy);
+    float *yd = dev_y ? y : nullptr, *xd = dev_x ? Hy : nullptr, *rd = nullptr;
+    double *partial = nullptr, *sums = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!dev_y) e = cudaMalloc((void**)&yd, (size_t)n * m * 4);
+    if (e == cudaSuccess && !dev_x) e = cudaMalloc((void**)&xd, (size_t)n * m * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&rd, (size_t)m * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&partial, (size_t)kDotBlocks * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&sums, 8);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rd, rhs, (size_t)m * 4, cudaMemcpyDefault, st);
+    probe_status s = (e == cudaSuccess) ? PROBE_OK : cuda_fail(h, e, "Krylov trial buffers");
+    const int grid = vec_grid(m);
+    for (int j = 0; j < n && s == PROBE_OK; ++j) {
+        const float* src = (j == 0) ? rd : xd + (long long)(j - 1) * m;
+        DotArgs args{};
+        args.a[0] = src;
+        args.b[0] = src;
+        k_dot_partial<<<kDotBlocks, kDotThreads, 0, st>>>(args, 1, m, partial);
+        k_dot_final<<<1, kDotThreads, 0, st>>>(partial, 1, kDotBlocks, sums);
+        k_scale_by_norm<<<grid, 256, 0, st>>>(yd + (long long)j * m, src, sums, m);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            s = cuda_fail(h, e, "Krylov normalisation");
+            break;
+        }
+        s = probe_apply_H(h, yd + (long long)j * m, xd + (long long)j * m, 1, stream);
+    }
+    if (s == PROBE_OK && !dev_y) e = cudaMemcpyAsync(y, yd, (size_t)n * m * 4, cudaMemcpyDeviceToHost, st);
+    if (s == PROBE_OK && e == cudaSuccess && !dev_x)
+        e = cudaMemcpyAsync(Hy, xd, (size_t)n * m * 4, cudaMemcpyDeviceToHost, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (s == PROBE_OK && (e != cudaSuccess || e2 != cudaSuccess))
+        s = cuda_fail(h, e != cudaSuccess ? e : e2, "Krylov trial copy");
+    if (!dev_y && yd) cudaFree(yd);
+    if (!dev_x && xd) cudaFree(xd);
+    if (rd) cudaFree(rd);
+    if (partial) cudaFree(partial);
+    if (sums) cudaFree(sums);
     return s;
 }

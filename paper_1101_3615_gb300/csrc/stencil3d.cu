@@ -65,7 +65,7 @@ __device__ __forceinline__ void load_pw3(const ModelStep3D& M, const float* outv
     if (MODE == STEP3_BORN || MODE == STEP3_ADJ) w.d = ld4(M.Din + (long long)shot * M.Din_shot_stride + off);
     if (MODE == STEP3_BORN) w.dm = ld4(M.dm + (long long)b * F + off);
     if (MODE == STEP3_ADJ) {
-        w.img = ld4(M.img + (long long)(shot * M.nfield + b) * F + off);
+        if (!M.seg_first) w.img = ld4(M.img + (long long)(shot * M.nfield + b) * F + off);
         if (KAHAN) w.cmp = ld4(M.comp + (long long)(shot * M.nfield + b) * F + off);
     }
 }
@@ -79,19 +79,20 @@ __device__ __forceinline__ void prefetch_pw3(const ModelStep3D& M, const float* 
     if (MODE == STEP3_BORN || MODE == STEP3_ADJ) prefetch_l2(M.Din + (long long)shot * M.Din_shot_stride + off);
     if (MODE == STEP3_BORN) prefetch_l2(M.dm + (long long)b * F + off);
     if (MODE == STEP3_ADJ) {
-        prefetch_l2(M.img + (long long)(shot * M.nfield + b) * F + off);
+        if (!M.seg_first) prefetch_l2(M.img + (long long)(shot * M.nfield + b) * F + off);
         if (KAHAN) prefetch_l2(M.comp + (long long)(shot * M.nfield + b) * F + off);
     }
 }
 
 // Update of one z plane of a thread's 4 cells, once every plane the taps need is in the ring:
 // slot_c holds the current plane (halo tile), slot_c -+ k the planes k below / above; cur_pw
-// the cells' pointwise operands; sinj the injection tile (adjoint, when inj).
+// the cells' pointwise operands; injv the receiver injection of the cells (adjoint, when inj).
 template <int MODE, bool KAHAN>
 __device__ __forceinline__ void cells3(const ModelStep3D& M, const float* smem, int slot_c, int lx, int ly, int x,
                                        int y, int z, long long off, int shot, int b, long long F, float* outv,
                                        const Pw3& cur_pw, const float4& Gc, const float4& Ac, int sz, int sy,
-                                       int sx, float fsrc, bool inj, const float* sinj) {
+                                       int sx, float fsrc, bool inj, float4 injv,
+                                       float4* dtt_out = nullptr, float4* prod_out = nullptr) {
     const float* cur = smem + slot_c * kPlane3;
     const float* rp = cur + (ly + 4) * kHX3 + lx + 4;
     const float4 a = ld4(rp - 4), c = ld4(rp), d = ld4(rp + 4);
@@ -155,11 +156,10 @@ __device__ __forceinline__ void cells3(const ModelStep3D& M, const float* smem, 
         Dv[2] = dd.z;
         Dv[3] = dd.w;
         if (inj) {
-            const float4 iv = ld4(sinj + ly * kTX + lx);
-            src[0] = iv.x;
-            src[1] = iv.y;
-            src[2] = iv.z;
-            src[3] = iv.w;
+            src[0] = injv.x;
+            src[1] = injv.y;
+            src[2] = injv.z;
+            src[3] = injv.w;
         }
     }
     const bool zin = (z >= M.pad) && (z < M.pad + M.nz);
@@ -179,16 +179,23 @@ __device__ __forceinline__ void cells3(const ModelStep3D& M, const float* smem, 
     st4(outv + off, make_float4(o[0], o[1], o[2], o[3]));
     if ((MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) && M.Dout)
         st4(M.Dout + (long long)shot * M.Dout_shot_stride + off, make_float4(Dw[0], Dw[1], Dw[2], Dw[3]));
+    if ((MODE == STEP3_INC || MODE == STEP3_INC_SAMPLE) && dtt_out) *dtt_out = make_float4(Dw[0], Dw[1], Dw[2], Dw[3]);
     if (MODE == STEP3_ADJ) {
-        float* ip = M.img + (long long)(shot * M.nfield + b) * F + off;
-        float4 iv = cur_pw.img;
         const float t0 = __fmul_rn(-Dv[0], o[0]), t1 = __fmul_rn(-Dv[1], o[1]);
         const float t2 = __fmul_rn(-Dv[2], o[2]), t3 = __fmul_rn(-Dv[3], o[3]);
+        if (prod_out) {  // the caller accumulates the image (shot-cluster kernel)
+            *prod_out = make_float4(t0, t1, t2, t3);
+            return;
+        }
+        float* ip = M.img + (long long)(shot * M.nfield + b) * F + off;
+        float4 iv = cur_pw.img;
         if (KAHAN) {
             float* cp = M.comp + (long long)(shot * M.nfield + b) * F + off;
             float4 cv = cur_pw.cmp;
             kahan4(iv, cv, t0, t1, t2, t3);
             st4(cp, cv);
+        } else if (M.seg_first) {
+            iv = make_float4(t0, t1, t2, t3);
         } else {
             iv.x = __fadd_rn(iv.x, t0);
             iv.y = __fadd_rn(iv.y, t1);
@@ -308,7 +315,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ 
         }
         if (col_ok && z < M.Nz)
             cells3<MODE, KAHAN>(M, smem, slot_c, lx, ly, x, y, z, off0 + (long long)iz * plane_stride, shot, b, F, outv,
-                                cur_pw, Gc, Ac, sz, sy, sx, fsrc, inj, sinj);
+                                cur_pw, Gc, Ac, sz, sy, sx, fsrc, inj,
+                                inj ? ld4(sinj + ly * kTX + lx) : make_float4(0.f, 0.f, 0.f, 0.f));
         __syncthreads();  // the slot of plane k = iz is free again
         if (tid == 0) {
             const int k = iz + kRing;
@@ -440,7 +448,7 @@ __global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_const
         }
         if (col_ok && z < M.Nz)
             cells3<MODE, false>(M, smem, slot_c, lx, ly, x, y, z, off0 + (long long)iz * plane_stride, shot, b, F,
-                                outv, cur_pw, Gc, Ac, sz, sy, sx, fsrc, false, nullptr);
+                                outv, cur_pw, Gc, Ac, sz, sy, sx, fsrc, false, make_float4(0.f, 0.f, 0.f, 0.f));
         __syncwarp();
         if (lane == 0) {  // this warp is done with plane k = iz (the bottom of its window)
             int sf = slot_c - 4;
@@ -458,6 +466,473 @@ __global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_const
 #pragma unroll 2
     for (int iz = 0; iz < nloc; ++iz)
         if (!plane(iz)) return;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Fused forward step (incident + Born trials) on a thread-block cluster.
+//
+// The cluster of one column tile and one shot holds 1 + nb CTAs: rank 0 advances the incident
+// field u0, rank 1 + b the Born field of trial b.  Each CTA streams its own field's halo'd planes
+// through its TMA ring (producer warp, per-slot full / empty mbarriers, as k_step3d_ws).  The
+// Born source needs Dtt u0^n of the same cells: rank 0 computes it in registers while updating
+// u0 and stores it straight into a small ring of Dtt planes in every Born CTA's shared memory
+// (distributed shared memory), then arrives on that slot's mbarrier in each of them; a Born CTA
+// releases the slot by arriving on rank 0's matching mbarrier.  Dtt u0 therefore never goes to
+// HBM: per cell and step the fused step moves u0^n, u0^{n-1}, s, u0^{n+1} and, per trial, du^n,
+// du^{n-1}, dm, du^{n+1} -- (16 + 16 nb) bytes instead of the 20 + 24 nb of separate incident
+// and Born launches.  The per-cell arithmetic is cells3, so the results are the same bits as
+// the separate launches.  Every wait is bounded; a CTA that gives up leaves its plane loop and
+// still meets the closing cluster barrier, so no CTA leaves while another can reach its shared
+// memory.
+// ---------------------------------------------------------------------------------------------
+constexpr int kDslots = 4;                 // Dtt planes in flight from rank 0 to the Born CTAs
+constexpr int kTile3 = kTY3 * kTX;          // cells of a column tile's plane
+constexpr int kMaxCluster3 = 8;             // portable cluster size: 1 + nb <= 8
+
+size_t fwd3d_cluster_smem_bytes() { return (size_t)kRing * kPlaneBytes3 + (size_t)kDslots * kTile3 * 4; }
+
+__global__ void __launch_bounds__(kWs3Threads, 2) k_fwd3d_cl(const __grid_constant__ StepParams3D p) {
+    extern __shared__ __align__(128) float smem[];  // [kRing][kPlane3] ring, then [kDslots][kTile3] Dtt
+    __shared__ __align__(8) uint64_t full[kRing], empty[kRing], dfull[kDslots], dempty[kDslots];
+    __shared__ int srec[kZC3D + 1];
+    const int nb = p.m2.nfield;
+    const int nf = nb + 1;
+    const uint32_t rank = cluster_ctarank();  // == blockIdx.x % nf: the field of this CTA
+    const bool inc = (rank == 0);
+    const ModelStep3D& M = inc ? p.m : p.m2;
+    const int b = inc ? 0 : (int)rank - 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int t = (int)(blockIdx.x / nf);
+    const int txi = t % M.tiles_x;
+    t /= M.tiles_x;
+    const int tyi = t % M.tiles_y;
+    const int zc = t / M.tiles_y;
+    const int x0 = txi * kTX, y0 = tyi * kTY3, z0 = zc * M.ZC;
+    const int zend = min(z0 + M.ZC, M.Nz);
+    const int shot = blockIdx.y;
+    const int n = p.n;
+    const int pc = n & 1, po = pc ^ 1;
+    const long long F = M.F;
+    const int vol_cur = shot * M.nvol_shot + 2 * b + pc;
+    float* outv = M.state + (long long)(shot * M.nvol_shot + 2 * b + po) * F;
+    const int nloc = zend - z0;
+    const int nplanes = nloc + 8;
+    float* dslots = smem + kRing * kPlane3;
+
+    if (tid == 0) {
+        for (int i = 0; i < kRing; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kThreads / 32);
+        }
+        for (int i = 0; i < kDslots; ++i) {
+            mbar_init(&dfull[i], 1);                      // armed for one plane of asynchronous stores
+            mbar_init(&dempty[i], (kThreads / 32) * nb);  // every Born CTA's consumer warps
+        }
+        if (!inc)
+            for (int i = 0; i < kDslots; ++i) mbar_arm_tx(&dfull[i], kTile3 * 4);
+        fence_mbar_init();
+    }
+    if (!inc && tid <= nloc) srec[tid] = M.rec_ptr[(tyi * M.tiles_x + txi) * M.Nz + z0 + tid];
+    __syncthreads();
+    cluster_sync_all();  // all barriers of the cluster exist before the first remote arrival
+    // after an earlier failure (a wait that gave up) the remaining CTAs do no work
+    const bool skip = *reinterpret_cast<volatile int*>(p.err) != 0;
+
+    if (warp == kThreads / 32) {  // ---------------- producer warp
+        if (lane == 0 && !skip) {
+            int sl = 0, issued = 0;
+            uint32_t eph = 0;
+            for (int k = 0; k < nplanes; ++k) {
+                if (k >= kRing && !mbar_wait_bounded(&empty[sl], eph)) {
+                    set_dev_error(p.err, DEVERR_TIMEOUT);
+                    break;
+                }
+                mbar_expect_tx(&full[sl], kPlaneBytes3);
+                tma_load_4d(smem + sl * kPlane3, &M.tm, x0 - 4, y0 - 4, z0 - 4 + k, vol_cur, &full[sl]);
+                ++issued;
+                if (++sl == kRing) {
+                    sl = 0;
+                    if (k + 1 >= 2 * kRing) eph ^= 1u;
+                }
+            }
+            // the last load of every slot must have landed before the CTA may exit
+            for (int q = max(0, issued - kRing); q < issued; ++q)
+                (void)mbar_wait_bounded(&full[q % kRing], (uint32_t)((q / kRing) & 1));
+        }
+    } else if (!skip) {  // ---------------- consumer warps
+        const int lx = (tid & 15) << 2, ly = tid >> 4;
+        const int x = x0 + lx, y = y0 + ly;
+        const bool col_ok = (x < M.Nx) && (y < M.Ny);
+        float4 Gc, Ac;
+        sponge_col3(M, y, x, Gc, Ac);
+        const int sz = inc ? M.src[3 * shot] : -1;
+        const int sy = inc ? M.src[3 * shot + 1] : -1;
+        const int sx = inc ? M.src[3 * shot + 2] : -1;
+        const float fsrc = inc ? M.wavelet[n] * M.vol_inv : 0.f;
+        const long long plane_stride = (long long)M.Ny * M.P;
+        const long long off0 = ((long long)z0 * M.Ny + y) * M.P + x;
+        const int cell = ly * kTX + lx;
+        const uint32_t dslot0 = smem_u32(dslots + cell);  // this thread's cells in Dtt slot 0
+        int slot_c = 4, slot_w = 8;
+        uint32_t ph_w = 0;
+        int dj = 0;
+        uint32_t dph = 0;  // Dtt slot and the parity of its current use
+        for (int iz = 0; iz < nloc; ++iz) {
+            const int z = z0 + iz;
+            const long long off = off0 + (long long)iz * plane_stride;
+            Pw3 cur_pw;
+            if (col_ok) {
+                cur_pw.s = ld4(M.s + off);
+                cur_pw.prev = ld4(outv + off);
+                if (!inc) cur_pw.dm = ld4(M.dm + (long long)b * F + off);
+                if (iz + kPrefetch3 < nloc) {
+                    const long long o2 = off + kPrefetch3 * plane_stride;
+                    prefetch_l2(M.s + o2);
+                    prefetch_l2(outv + o2);
+                    if (!inc) prefetch_l2(M.dm + (long long)b * F + o2);
+                }
+            }
+            bool ok = true;
+            const int kfirst = (iz == 0) ? 0 : iz + 8;
+            for (int k = kfirst; k <= iz + 8 && ok; ++k)
+                ok = (iz == 0) ? mbar_wait_bounded(&full[k], 0u) : mbar_wait_bounded(&full[slot_w], ph_w);
+            if (inc) {
+                // the Born CTAs are done with the previous contents of Dtt slot dj
+                if (ok && iz >= kDslots) ok = mbar_wait_bounded(&dempty[dj], dph ^ 1u);
+                if (!ok) {
+                    set_dev_error(p.err, DEVERR_TIMEOUT);
+                    break;
+                }
+                float4 dw = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (col_ok)
+                    cells3<STEP3_INC, false>(M, smem, slot_c, lx, ly, x, y, z, off, shot, 0, F, outv, cur_pw, Gc, Ac,
+                                             sz, sy, sx, fsrc, false, make_float4(0.f, 0.f, 0.f, 0.f), &dw, nullptr);
+                // every thread stores its 16 bytes (zeros off the grid) so that each Born CTA's
+                // slot barrier receives exactly one plane, kTile3 * 4 bytes
+                const uint32_t la = dslot0 + (uint32_t)(dj * kTile3 * 4);
+                const uint32_t lb = smem_u32(&dfull[dj]);
+                for (int r = 1; r <= nb; ++r) st_async4(mapa_rank(la, (uint32_t)r), dw, mapa_rank(lb, (uint32_t)r));
+            } else {
+                if (ok) {  // receivers of this plane, from its staged tile
+                    const int rbeg = srec[iz], rend = srec[iz + 1];
+                    if (rend > rbeg) {
+                        const float* cur = smem + slot_c * kPlane3;
+                        float* dout = M.data + (long long)shot * M.dss + (long long)b * M.dts + (long long)n * M.nr;
+                        for (int i = rbeg + tid; i < rend; i += kThreads) {
+                            const int r = M.rec_idx[i];
+                            dout[r] = cur[(M.rec_zyx[3 * r + 1] - y0 + 4) * kHX3 + (M.rec_zyx[3 * r + 2] - x0 + 4)];
+                        }
+                    }
+                }
+                if (ok) ok = mbar_wait_bounded(&dfull[dj], dph);
+                if (!ok) {
+                    set_dev_error(p.err, DEVERR_TIMEOUT);
+                    break;
+                }
+                // this slot's next plane: arm its barrier once the present one has completed
+                if (tid == 0 && iz + kDslots < nloc) mbar_arm_tx(&dfull[dj], kTile3 * 4);
+                if (col_ok) {
+                    cur_pw.d = ld4(dslots + dj * kTile3 + cell);
+                    cells3<STEP3_BORN, false>(M, smem, slot_c, lx, ly, x, y, z, off, shot, b, F, outv, cur_pw, Gc,
+                                              Ac, -1, -1, -1, 0.f, false, make_float4(0.f, 0.f, 0.f, 0.f), nullptr,
+                                              nullptr);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(mapa_rank(smem_u32(&dempty[dj]), 0u));
+            }
+            __syncwarp();
+            if (lane == 0) {  // this warp is done with plane k = iz (the bottom of its window)
+                int sf = slot_c - 4;
+                sf += (sf < 0) ? kRing : 0;
+                mbar_arrive(&empty[sf]);
+            }
+            slot_c = (slot_c + 1 == kRing) ? 0 : slot_c + 1;
+            if (++slot_w == kRing) {
+                slot_w = 0;
+                ph_w ^= 1u;
+            }
+            if (++dj == kDslots) {
+                dj = 0;
+                dph ^= 1u;
+            }
+        }
+    }
+    __syncwarp();
+    cluster_sync_all();  // no CTA of the cluster leaves while another may still reach its memory
+}
+
+cudaError_t launch_fwd3d_cluster(const StepParams3D& p, cudaStream_t st) {
+    const ModelStep3D& M = p.m2;
+    const int nf = M.nfield + 1;
+    if (nf < 2 || nf > kMaxCluster3) return cudaErrorInvalidValue;
+    dim3 grid(M.tiles_x * M.tiles_y * M.zchunks * nf, M.nshots);
+    if (grid.y == 0) return cudaSuccess;
+    const size_t sm = fwd3d_cluster_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_fwd3d_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kWs3Threads, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)nf;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fwd3d_cl, p);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Adjoint step with imaging on a cluster of G shots.
+//
+// A cluster holds the CTAs of one column tile and one trial for G consecutive shots of a wave
+// (cluster rank = shot within the group).  Each CTA advances its shot's adjoint field exactly as
+// k_step3d<ADJ> (same per-cell arithmetic, cells3) and forms its imaging term
+// t_s = -Dtt u_s^{n-1} mu_s^n.  The image of the group is updated once per plane instead of once
+// per shot: plane iz belongs to rank o = iz mod G, every other rank stores its t_s for that plane
+// into rank o's reduction slot (distributed shared memory) with asynchronous stores that complete
+// on o's slot barrier; rank o sums the G terms in rank order and applies one Kahan-compensated
+// update to the group image [group][trial] in HBM, then releases the slot (plain arrivals).  Per cell, step and (shot, trial) the image
+// read-modify-write (16 bytes with Kahan) thus costs 16/G bytes.  The receiver injection R^T r^n
+// comes from the segment's prebuilt buffer of the planes that hold receivers (one float4 per
+// thread on those planes), so no barrier of the whole CTA is taken.  Every wait is bounded.
+// ---------------------------------------------------------------------------------------------
+// Reduction planes per CTA: (G - 1) contributor planes for each of R slots (R = 1: a rank may run at
+// most G planes ahead of the owner that last read its slot).  G = 1 and 2 keep the shared memory
+// of a CTA within a third of the SM's, so three CTAs (27 warps) share an SM, as for the one-field
+// kernels; G = 4 and 8 fit two.
+template <int G>
+struct AdjCl {
+    static constexpr int R = 1;
+    static constexpr int kRed = (G - 1) * R;
+    static constexpr int kMinBlocks = (G <= 2) ? 3 : 2;
+};
+
+size_t adj3d_cluster_smem_bytes(int G) { return (size_t)kRing * kPlaneBytes3 + (size_t)(G - 1) * kTile3 * 4; }
+
+template <int G, bool KAHAN>
+__global__ void __launch_bounds__(kWs3Threads, AdjCl<G>::kMinBlocks) k_adj3d_cl(const __grid_constant__ StepParams3D p) {
+    constexpr int R = AdjCl<G>::R;  // reduction slots per owner
+    extern __shared__ __align__(128) float smem[];  // ring, then reduction planes [R][G - 1][kTile3]
+    __shared__ __align__(8) uint64_t full[kRing], empty[kRing], rfull[R], wok[G][R];
+    __shared__ int sband[kZC3D];  // receiver plane (band) index of each plane of the chunk, -1 without
+    const ModelStep3D& M = p.m;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b = (int)(blockIdx.x % M.nfield);
+    int t = (int)(blockIdx.x / M.nfield);
+    const int txi = t % M.tiles_x;
+    t /= M.tiles_x;
+    const int tyi = t % M.tiles_y;
+    const int zc = t / M.tiles_y;
+    const int x0 = txi * kTX, y0 = tyi * kTY3, z0 = zc * M.ZC;
+    const int zend = min(z0 + M.ZC, M.Nz);
+    const int shot = blockIdx.y;
+    const int crank = (G > 1) ? (int)cluster_ctarank() : 0;  // == shot % G
+    const int grp = shot / G;
+    const int n = p.n;
+    const int pc = (n + 1) & 1, po = pc ^ 1;
+    const long long F = M.F;
+    const int vol_cur = shot * M.nvol_shot + 2 * b + pc;
+    float* outv = M.state + (long long)(shot * M.nvol_shot + 2 * b + po) * F;
+    float* imgp = M.img + (long long)(grp * M.nfield + b) * F;
+    float* cmpp = M.comp + (long long)(grp * M.nfield + b) * F;
+    const int nloc = zend - z0;
+    const int nplanes = nloc + 8;
+    float* red = smem + kRing * kPlane3;
+
+    if (tid == 0) {
+        for (int i = 0; i < kRing; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kThreads / 32);
+        }
+        for (int j = 0; j < R; ++j) {
+            mbar_init(&rfull[j], 1);  // armed for the G - 1 other ranks' asynchronous stores of one plane
+            if (G > 1) mbar_arm_tx(&rfull[j], (G - 1) * kTile3 * 4);
+            for (int o = 0; o < G; ++o) mbar_init(&wok[o][j], kThreads / 32);  // rank o's consumer warps
+        }
+        fence_mbar_init();
+    }
+    if (tid < nloc) sband[tid] = M.rrow ? M.rrow[z0 + tid] : -1;
+    __syncthreads();
+    if (G > 1) cluster_sync_all();
+    const bool skip = *reinterpret_cast<volatile int*>(p.err) != 0;
+
+    if (warp == kThreads / 32) {  // ---------------- producer warp
+        if (lane == 0 && !skip) {
+            int sl = 0, issued = 0;
+            uint32_t eph = 0;
+            for (int k = 0; k < nplanes; ++k) {
+                if (k >= kRing && !mbar_wait_bounded(&empty[sl], eph)) {
+                    set_dev_error(p.err, DEVERR_TIMEOUT);
+                    break;
+                }
+                mbar_expect_tx(&full[sl], kPlaneBytes3);
+                tma_load_4d(smem + sl * kPlane3, &M.tm, x0 - 4, y0 - 4, z0 - 4 + k, vol_cur, &full[sl]);
+                ++issued;
+                if (++sl == kRing) {
+                    sl = 0;
+                    if (k + 1 >= 2 * kRing) eph ^= 1u;
+                }
+            }
+            for (int q = max(0, issued - kRing); q < issued; ++q)
+                (void)mbar_wait_bounded(&full[q % kRing], (uint32_t)((q / kRing) & 1));
+        }
+    } else if (!skip) {  // ---------------- consumer warps
+        const int lx = (tid & 15) << 2, ly = tid >> 4;
+        const int x = x0 + lx, y = y0 + ly;
+        const bool col_ok = (x < M.Nx) && (y < M.Ny);
+        float4 Gc, Ac;
+        sponge_col3(M, y, x, Gc, Ac);
+        const long long plane_stride = (long long)M.Ny * M.P;
+        const long long off0 = ((long long)z0 * M.Ny + y) * M.P + x;
+        const float* Din = M.Din + (long long)shot * M.Din_shot_stride;
+        const int cell = ly * kTX + lx;
+        const long long plane_cells = (long long)M.Ny * M.P;  // one band plane of the injection buffer
+        const float* injp = M.inj + ((long long)(M.inj_slot * M.nshots + shot) * M.nfield + b) * M.inj_block +
+                            (long long)y * M.P + x;
+        int slot_c = 4, slot_w = 8;
+        uint32_t ph_w = 0;
+        for (int iz = 0; iz < nloc; ++iz) {
+            const int z = z0 + iz;
+            const long long off = off0 + (long long)iz * plane_stride;
+            const int owner = iz % G;
+            const bool own = (owner == crank);
+            const int kk = iz / G;              // the owner's kk-th plane
+            const int j = kk % R;               // its reduction slot
+            const uint32_t use = (uint32_t)(kk / R);
+            Pw3 cur_pw;
+            if (col_ok) {
+                cur_pw.s = ld4(M.s + off);
+                cur_pw.prev = ld4(outv + off);
+                cur_pw.d = ld4(Din + off);
+                if (own) {
+                    cur_pw.img = ld4(imgp + off);
+                    if (KAHAN) cur_pw.cmp = ld4(cmpp + off);
+                }
+                if (iz + kPrefetch3 < nloc) {
+                    const long long o2 = off + kPrefetch3 * plane_stride;
+                    prefetch_l2(M.s + o2);
+                    prefetch_l2(outv + o2);
+                    prefetch_l2(Din + o2);
+                    if ((iz + kPrefetch3) % G == crank) {
+                        prefetch_l2(imgp + o2);
+                        if (KAHAN) prefetch_l2(cmpp + o2);
+                    }
+                }
+            }
+            bool ok = true;
+            const int kfirst = (iz == 0) ? 0 : iz + 8;
+            for (int k = kfirst; k <= iz + 8 && ok; ++k)
+                ok = (iz == 0) ? mbar_wait_bounded(&full[k], 0u) : mbar_wait_bounded(&full[slot_w], ph_w);
+            if (!ok) {
+                set_dev_error(p.err, DEVERR_TIMEOUT);
+                break;
+            }
+            const int band = sband[iz];
+            const bool inj = band >= 0;
+            const float4 injv = (inj && col_ok) ? ld4(injp + band * plane_cells) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 tv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (col_ok)
+                cells3<STEP3_ADJ, KAHAN>(M, smem, slot_c, lx, ly, x, y, z, off, shot, b, F, outv, cur_pw, Gc, Ac, -1,
+                                         -1, -1, 0.f, inj, injv, nullptr, &tv);
+            if (!own) {  // hand the term to the plane's owner (16 bytes per thread, zeros off the grid)
+                if (use > 0 && !mbar_wait_bounded(&wok[owner][j], (use - 1u) & 1u)) {
+                    set_dev_error(p.err, DEVERR_TIMEOUT);
+                    break;
+                }
+                const int slot = j * (G - 1) + (crank < owner ? crank : crank - 1);  // contributor plane
+                st_async4(mapa_rank(smem_u32(red + slot * kTile3 + cell), (uint32_t)owner), tv,
+                          mapa_rank(smem_u32(&rfull[j]), (uint32_t)owner));
+            } else {
+                if (G > 1 && !mbar_wait_bounded(&rfull[j], use & 1u)) {
+                    set_dev_error(p.err, DEVERR_TIMEOUT);
+                    break;
+                }
+                // the slot's next use (G R planes on): arm once the present one has completed
+                if (G > 1 && tid == 0 && iz + G * R < nloc) mbar_arm_tx(&rfull[j], (G - 1) * kTile3 * 4);
+                if (col_ok) {
+                    const float* rj = red + j * (G - 1) * kTile3 + cell;
+                    float4 sum = (crank == 0) ? tv : ld4(rj);  // terms in rank order
+#pragma unroll
+                    for (int c = 1; c < G; ++c) {
+                        const float4 v = (c == crank) ? tv : ld4(rj + (c < crank ? c : c - 1) * kTile3);
+                        sum.x = __fadd_rn(sum.x, v.x);
+                        sum.y = __fadd_rn(sum.y, v.y);
+                        sum.z = __fadd_rn(sum.z, v.z);
+                        sum.w = __fadd_rn(sum.w, v.w);
+                    }
+                    float4 iv = cur_pw.img;
+                    if (KAHAN) {
+                        float4 cv = cur_pw.cmp;
+                        kahan4(iv, cv, sum.x, sum.y, sum.z, sum.w);
+                        st4(cmpp + off, cv);
+                    } else {
+                        iv.x = __fadd_rn(iv.x, sum.x);
+                        iv.y = __fadd_rn(iv.y, sum.y);
+                        iv.z = __fadd_rn(iv.z, sum.z);
+                        iv.w = __fadd_rn(iv.w, sum.w);
+                    }
+                    st4(imgp + off, iv);
+                }
+                if (G > 1) {
+                    __syncwarp();
+                    if (lane == 0)
+                        for (int c = 0; c < G; ++c)
+                            if (c != crank) mbar_arrive_remote(mapa_rank(smem_u32(&wok[crank][j]), (uint32_t)c));
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                int sf = slot_c - 4;
+                sf += (sf < 0) ? kRing : 0;
+                mbar_arrive(&empty[sf]);
+            }
+            slot_c = (slot_c + 1 == kRing) ? 0 : slot_c + 1;
+            if (++slot_w == kRing) {
+                slot_w = 0;
+                ph_w ^= 1u;
+            }
+        }
+    }
+    __syncwarp();
+    if (G > 1) cluster_sync_all();
+}
+
+template <int G, bool KAHAN>
+static cudaError_t launch_adj3d_cl_t(const StepParams3D& p, cudaStream_t st) {
+    const ModelStep3D& M = p.m;
+    dim3 grid(M.tiles_x * M.tiles_y * M.zchunks * M.nfield, M.nshots);
+    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+    if (grid.y % G) return cudaErrorInvalidValue;
+    const size_t sm = adj3d_cluster_smem_bytes(G);
+    cudaError_t e = cudaFuncSetAttribute(k_adj3d_cl<G, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kWs3Threads, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = (unsigned)G;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_adj3d_cl<G, KAHAN>, p);
+}
+
+cudaError_t launch_adj3d_cluster(int G, bool kahan, const StepParams3D& p, cudaStream_t st) {
+    switch (G) {
+        case 1: return kahan ? launch_adj3d_cl_t<1, true>(p, st) : launch_adj3d_cl_t<1, false>(p, st);
+        case 2: return kahan ? launch_adj3d_cl_t<2, true>(p, st) : launch_adj3d_cl_t<2, false>(p, st);
+        case 4: return kahan ? launch_adj3d_cl_t<4, true>(p, st) : launch_adj3d_cl_t<4, false>(p, st);
+        case 8: return kahan ? launch_adj3d_cl_t<8, true>(p, st) : launch_adj3d_cl_t<8, false>(p, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int MODE>

@@ -19,10 +19,10 @@ def _parse(argv):
 
 def test_defaults_follow_the_timing_contract():
     a = _parse([])
-    assert a.gpus == 1 and a.config == 2 and a.impl == "ours"
+    assert a.gpus == 1 and a.config == 5 and a.impl == "ours"   # the largest single-GPU configuration
     assert a.warmup >= 3 and a.steps >= 1
-    assert a.snapshot == "fp16"
-    assert _parse(["--config", "5"]).snapshot == "bf16"          # the configuration's own
+    assert a.snapshot == "bf16"                                  # the configuration's own
+    assert _parse(["--config", "2"]).snapshot == "fp16"
     assert _parse(["--config", "5", "--snapshot", "fp32"]).snapshot == "fp32"
 
 
@@ -30,6 +30,7 @@ def test_kernel_labels_name_the_source_files():
     assert bench.kernel_label(3, False)[1] == "stencil2d_pipe.cu"
     assert bench.kernel_label(0, True)[1] == "stencil2d.cu"
     assert bench.kernel_label(0, False, ndim=3)[1] == "stencil3d.cu"
+    assert "k_adj3d_cl<G=4" in bench.kernel_label(0, True, ndim=3, cluster=True, group=4)[0]
     for args in ((3, False), (2, True), (0, False), (0, True)):
         name, src = bench.kernel_label(*args)
         assert os.path.exists(os.path.join(bench.ROOT, "paper_1101_3615_gb300", "csrc", src))

@@ -1,10 +1,13 @@
 """GPU parity of probe_fit / probe_apply_precond with the FP64 oracle (needs a GB300).
 
-Both sides receive the same FP32 arrays.  The GPU forms the normal equations
-of Sec. 1.4 in FP64 and solves them by Cholesky; the oracle uses Householder
-QR of the stacked columns.  Bars: coefficients within 1e-6 (relative L2) of
-the oracle's, preconditioned images within 1e-6, exact recovery of known
-coefficients limited only by the FP32 rounding of the inputs (1e-5).
+Both sides receive the same FP32 arrays.  The GPU solves the least-squares
+problem of Sec. 1.4 through a CholeskyQR2 factorisation of the stacked columns
+in FP64; the oracle uses Householder QR.  Bars: coefficients within 1e-6
+(relative L2) of the oracle's -- also on bases with cond(A) of 1e6 to 1e7,
+where the normal equations alone would lose about cond(A)^2 eps = 1e-2 -- and
+on the largest basis (P = 1024); preconditioned images within 1e-6; exact
+recovery of known coefficients limited only by the FP32 rounding of the inputs
+(1e-5).
 """
 import numpy as np
 import pytest
@@ -26,10 +29,10 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def bases(wl, spatial=SPATIAL5, angular=ANG4, nradial=2, order=-1.0, fft_pad=16):
+def bases(wl, spatial=SPATIAL5, angular=ANG4, nradial=2, order=-1.0, fft_pad=16, lf=30.0):
     from paper_1101_3615_gb300 import Basis
     c_mean = float(np.mean(1 / np.sqrt(wl.m0.astype(np.float64))))
-    L = 2 * np.pi * 30.0 / c_mean
+    L = 2 * np.pi * lf / c_mean
     g = Basis(wl.ndim, spatial, angular, nradial, L, order, fft_pad)
     o = OBasis(wl.shape, wl.h, spatial, angular, nradial, L, order, fft_pad)
     return g, o
@@ -91,7 +94,7 @@ def test_fit_errors(cuda_device):
     wl = mini_config(1, shape=(40, 44), nt=50, ns=1)
     p = make_probe(wl)
     y = torch.tensor(bandpassed_noise(wl.m0, wl.h, 1, p=1), device=cuda_device)
-    too_many = Basis(2, [(0, 0)] * 9, [0, 2, -2, 4], 2, 0.05)   # P = 72 > 64
+    too_many = Basis(2, [(0, 0)] * 33, [0, 2, -2, 4], 2, 0.05)  # more than 32 spatial modes
     with pytest.raises(ProbeError) as ei:
         p.fit(too_many, y, y)
     assert ei.value.status == -1
@@ -99,3 +102,36 @@ def test_fit_errors(cuda_device):
     with pytest.raises(ProbeError) as ei:
         p.fit(dup, y, y)
     assert ei.value.status == -6
+
+
+# A small basis (P = 64, Gram in one CTA) and a large one (P = 160, chunked Gram), both with
+# cond(A) of about 1e6 - 2e6 on these band-limited trials (eight Chebyshev terms on a narrow band)
+@pytest.mark.parametrize("spatial,nradial", [([(0, 0), (0, 1)], 8), (SPATIAL5, 8)])
+def test_fit_ill_conditioned_basis_matches_qr(cuda_device, spatial, nradial):
+    wl = mini_config(1, shape=(48, 52), nt=50, ns=1)
+    g, o = bases(wl, spatial=spatial, nradial=nradial, fft_pad=8, lf=60.0)
+    c_true = np.random.default_rng(5).standard_normal(g.P)
+    xs = bandpassed_noise(wl.m0, wl.h, 4242, p=2)
+    ys = np.stack([o.apply(c_true, xj.astype(np.float64)) for xj in xs]).astype(np.float32)
+    c_orc, res_orc, cond = ofit(o, ys, xs)
+    assert cond > 1e6                                            # the regime the QR is for
+    p = make_probe(wl)
+    c_gpu, res_gpu = p.fit(g, torch.tensor(ys, device=cuda_device), torch.tensor(xs, device=cuda_device))
+    assert rel(c_gpu, c_orc) < 1e-6, cond
+    assert abs(res_gpu - res_orc) < 1e-7
+
+
+def test_fit_largest_basis(cuda_device):
+    """P = 32 spatial modes x 8 angular x 4 radial = 1024 terms, four trials: exact recovery."""
+    wl = mini_config(1, shape=(96, 100), nt=50, ns=1)
+    sp = [(a, b) for a in range(-3, 4) for b in range(-3, 4)][:32]
+    g, o = bases(wl, spatial=sp, angular=[0, 2, -2, 4, -4, 6, -6, 8], nradial=4, fft_pad=8)
+    assert g.P == 1024
+    c_true = np.random.default_rng(5).standard_normal(g.P)
+    xs = bandpassed_noise(wl.m0, wl.h, 4242, p=4)
+    ys = np.stack([o.apply(c_true, xj.astype(np.float64)) for xj in xs]).astype(np.float32)
+    c_orc, res_orc, cond = ofit(o, ys, xs)
+    p = make_probe(wl)
+    c_gpu, res_gpu = p.fit(g, torch.tensor(ys, device=cuda_device), torch.tensor(xs, device=cuda_device))
+    assert rel(c_gpu, c_orc) < 1e-6, cond
+    assert rel(c_gpu, c_true) < 1e-5, cond

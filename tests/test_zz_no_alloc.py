@@ -7,8 +7,9 @@ synchronise the device.  For them the library offers an allocation-free
 variant of the Born forward whose per-call scratch is a fixed static device
 array.  This file checks it through the C ABI against the regular entry point,
 on two calls in a row (the shared scratch keeps the previous call's contents),
-with shots split into several waves, and checks that a problem too large for
-the static scratch is refused on the host.
+with shots split into several waves, that the second call leaves the device's
+free memory unchanged, and that a problem too large for the static scratch is
+refused on the host.
 """
 import ctypes as C
 
@@ -52,8 +53,14 @@ def test_noalloc_matches_apply_F_on_two_calls(cuda_device):
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     for call in range(2):
         out = torch.full((2, wl.ns, wl.nt, wl.nr), float("nan"), device=cuda_device)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         st = fn(p.handle, C.c_void_p(dm.data_ptr()), C.c_void_p(out.data_ptr()), 2, stream)
+        torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info()[0]
         assert st == 0, (call, st)
+        if call == 1:  # the first call may load kernels lazily; the second must leave free memory alone
+            assert free_after == free_before, (free_before, free_after)
         got = out.cpu().numpy()
         assert np.all(np.isfinite(got))
         for b in range(2):

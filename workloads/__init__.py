@@ -17,6 +17,7 @@ from .synth import (  # noqa: F401
     bandpassed_noise,
     random_sign_trials,
     gaussian_bumps,
+    white_noise_trials,
     make_config,
     data_noise,
     mini_config,

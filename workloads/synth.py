@@ -216,6 +216,13 @@ def random_sign_trials(m0, h, seed, p=8, f_lo=5.0, f_hi=25.0) -> np.ndarray:
     return np.stack(out).astype(np.float32)
 
 
+def white_noise_trials(m0, seed, p=1) -> np.ndarray:
+    """p fields of iid N(0,1) noise on the interior, scaled like the other trials (the input of
+    the H-applied white-noise trial functions y = H n)."""
+    rng = _rng(seed)
+    return np.stack([_normalise(rng.standard_normal(m0.shape), m0) for _ in range(p)]).astype(np.float32)
+
+
 def gaussian_bumps(shape, h, seed, n=200, sigma_m=16.0, amp=1.0) -> np.ndarray:
     """Sum of n random-sign Gaussian bumps exp(-|x-x_k|^2 / 2 sigma^2) * amp.
 
