@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=5)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="stop after the timed steps and print their line (no breakdown, e2e, dot test, plain, "
+                         "precond or CPU legs): the command whose kernel launches an ncu launch list records")
+    ap.add_argument("--tblock", type=int, default=0, help="2D: time levels per launch (1 or 2; 0: autotuned)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-history", action="store_true",
                     help="skip the extra measurement with the full Dtt history resident")
@@ -117,12 +121,15 @@ def profile_run(a, wl):
         p.set_option("cluster3d", a.cluster3d)
     if a.shot_group > 0:
         p.set_option("shot_group", a.shot_group)
+    if a.tblock and len(wl.shape) == 2:
+        p.set_option("tblock", a.tblock)
     dm = torch.tensor(wl.trials, device=dev)
     if a.profile == "fwd":
         run = lambda: p.apply_F(dm)
-    else:
-        d = torch.zeros((1, wl.ns, wl.nt, wl.nr), device=dev)
-        d[0, :, :, :] = 1e-3 * torch.randn((wl.ns, wl.nt, wl.nr), device=dev)
+    else:  # as many data sets as the workload has trials (the H application's adjoint)
+        ntr = wl.trials.shape[0]
+        g = torch.Generator(device=dev).manual_seed(1234)
+        d = 1e-3 * torch.randn((ntr, wl.ns, wl.nt, wl.nr), device=dev, generator=g)
         run = lambda: p.apply_Fadj(d)
     run()
     torch.cuda.synchronize()
@@ -240,15 +247,19 @@ def kernel_source_hash(name):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def kernel_label(pipeline, adjoint, ndim=2, cluster=True, group=1):
+def kernel_label(pipeline, adjoint, ndim=2, cluster=False, group=1, time_block=0):
     """Kernel name and source file of the forward / adjoint step variant the handle ran."""
+    if ndim == 2 and time_block and not adjoint:
+        return ("k_fwd2d_tb<FWD_BORN> (incident + Born fields advanced two time levels per launch)",
+                "stencil2d.cu")
     if ndim == 3:
         if cluster:
             return ((f"k_adj3d_cl<G={group}, kahan> (adjoint + imaging; the images of a {group}-shot cluster "
                      "summed in distributed shared memory before one Kahan update)" if adjoint else
                      "k_fwd3d_cl (incident + Born fields of a column tile on a cluster of 1 + p CTAs, "
                      "Dtt u0 exchanged in distributed shared memory)"), "stencil3d.cu")
-        return (("k_step3d<ADJ, kahan>" if adjoint else
+        return (("k_step3d<ADJ> (adjoint + imaging into checkpoint-segment images, Kahan fold per segment)"
+                 if adjoint else
                  "k_step3d_ws<BORN> / <INC> (3D forward steps, one field kind per launch)"), "stencil3d.cu")
     if pipeline:
         name = (f"k_adj2d_ws<nbc, kahan, S={pipeline}>" if adjoint else
@@ -438,14 +449,15 @@ def _sync_time(torch, fn):
     return out, time.perf_counter() - t
 
 
-# Symbol bases of growing size (spatial modes, angular harmonics, radial terms): P = 4 ... 1000.
+# Symbol bases of growing size (spatial modes, angular harmonics, radial terms): P = 4 ... 1024.
 def _trial_bases():
     s1 = [(0, 0)]
     s5 = [(0, 0), (0, 1), (0, -1), (1, 0), (-1, 0)]
     s9 = [(a, b) for a in (-1, 0, 1) for b in (-1, 0, 1)]
     s25 = [(a, b) for a in range(-2, 3) for b in range(-2, 3)]
     a4, a5, a8 = [0, 2, -2, 4], [0, 2, -2, 4, -4], [0, 2, -2, 4, -4, 6, -6, 8]
-    return [(s1, a4, 1), (s5, a4, 1), (s5, a4, 3), (s9, a5, 4), (s25, a5, 4), (s25, a8, 5)]
+    s32 = (s25 + [(a, b) for a in (-3, 3) for b in (-1, 0, 1)] + [(0, 3)])[:32]
+    return [(s1, a4, 1), (s5, a4, 1), (s5, a4, 3), (s9, a5, 4), (s25, a5, 4), (s32, a8, 4)]
 
 
 def experiment_trials(a):
@@ -458,7 +470,7 @@ def experiment_trials(a):
 
     import __graft_entry__ as ge
     ge._build_module().build()
-    from paper_1101_3615_gb300 import Basis
+    from paper_1101_3615_gb300 import Basis, ProbeError
     from workloads import make_config, random_sign_trials, white_noise_trials
     wl = make_config(2)
     dev = torch.device("cuda", 0)
@@ -489,13 +501,18 @@ def experiment_trials(a):
     fam["white"] = (yw, H(yw))
     yt = torch.tensor(random_sign_trials(wl.m0, wl.h, 2199, p=1), device=dev)
     xt = H(yt)[0].contiguous()
-    Ps, mse, fit_ms = [], {k: [] for k in fam}, []
+    Ps, mse, fit_ms, rank_deficient = [], {k: [] for k in fam}, [], []
     for sp, ang, nrad in _trial_bases():
         b = Basis(2, sp, ang, nrad, L, -1.0, 16)
         Ps.append(b.P)
         tf = 0.0
         for k, (yy, xx) in fam.items():
-            (c, _), dt = _sync_time(torch, lambda: p.fit(b, yy, xx))
+            try:
+                (c, _), dt = _sync_time(torch, lambda: p.fit(b, yy, xx))
+            except ProbeError as ex:  # columns numerically rank deficient for this family and basis
+                mse[k].append(None)
+                rank_deficient.append([k, b.P, str(ex)[:80]])
+                continue
             tf += dt
             pre = p.apply_precond(b, c, xt)
             mse[k].append(float(torch.linalg.vector_norm((pre - yt[0]).double()) /
@@ -503,7 +520,7 @@ def experiment_trials(a):
         fit_ms.append(tf / len(fam) * 1e3)
     print(json.dumps({
         "experiment": "trial_functions", "workload": "2d-501x501-nt2500-32shots", "trials_per_family": npf,
-        "P": Ps, "generalisation_mse": mse, "fit_ms_mean": fit_ms,
+        "P": Ps, "generalisation_mse": mse, "fit_ms_mean": fit_ms, "rank_deficient": rank_deficient,
         "h_applies": n_h, "ms_per_h_apply": t_h / max(n_h, 1) * 1e3, "krylov_ms": tk * 1e3,
         "how": "fit of sum_i c_i B_i ~ H^{-1} on (y_j, H y_j) of each family (CholeskyQR2, FP64), then "
                "||y_t - M(H y_t)|| / ||y_t|| on an independent random-sign trial y_t; Kn from F*d of the "
@@ -716,6 +733,12 @@ def main():
         pf, pa, rows, grp = (int(v) for v in a.fixed.split(","))
         for k, v in (("pipeline", pf), ("pipeline_adj", pa), ("pipe_rows", rows), ("shot_group", grp)):
             p.set_option(k, v)
+    if is3d and a.cluster3d >= 0:
+        p.set_option("cluster3d", a.cluster3d)
+    if a.shot_group > 0:
+        p.set_option("shot_group", a.shot_group)
+    if a.tblock and not is3d:
+        p.set_option("tblock", a.tblock)
     dm = torch.tensor(wl.trials, device=dev)
     out = torch.empty_like(dm)
     stream = torch.cuda.current_stream(dev)
@@ -746,6 +769,12 @@ def main():
     ms_step = ms_total / a.steps
     value = weak_scaling_value(cells_per_h, world, ms_step) / 1e9
     h_per_s = weak_scaling_value(wl.trials.shape[0], world, ms_step)
+    if a.only_timed:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "steps": a.steps, "warmup": a.warmup,
+                              "ms_per_step": ms_step, "h_applies_per_s": h_per_s, "only_timed": True,
+                              "config": {"workload": CONFIG_NAMES[a.config]}, "stats": p.stats()}))
+        return
     # forward-sweep CUDA-event time and launch counts of the last timed step (same stream)
     stats = p.stats()
     fwd_ms, fwd_b, fwd_l = stats["ms_forward"], stats["bytes_forward"], stats["launches_forward"]
@@ -918,9 +947,11 @@ def main():
         del ps, ys
 
     live_mb = wl.ns * (2 + 2 * ntr) * wl.cells_padded() * 4 / 1e6
-    cl = bool(is3d)
-    fwd_name, fwd_src = kernel_label(stats["pipeline_forward"], False, len(wl.shape), cl, stats["shot_group"])
-    adj_name, adj_src = kernel_label(stats["pipeline_adjoint"], True, len(wl.shape), cl, stats["shot_group"])
+    cl = max(a.cluster3d, 0) if is3d else 0  # 3D cluster kernels only when asked for (library default 0)
+    fwd_name, fwd_src = kernel_label(stats["pipeline_forward"], False, len(wl.shape), bool(cl & 1),
+                                     stats["shot_group"], stats["time_block"])
+    adj_name, adj_src = kernel_label(stats["pipeline_adjoint"], True, len(wl.shape), bool(cl & 2),
+                                     stats["shot_group"])
     if is3d:
         fwd_var = {"shot_wave": stats["shot_wave"], "trials": ntr}
         adj_var = {"shot_wave": stats["shot_wave"], "shot_group": stats["shot_group"], "trials": ntr}
@@ -928,7 +959,8 @@ def main():
         adj_traffic = ncu_traffic("adj3d", adj_src, adj_var)
     else:
         fwd_traffic = ncu_traffic("fwd_born", fwd_src, {"pipeline_forward": stats["pipeline_forward"],
-                                                        "pipeline_rows": stats["pipeline_rows"]})
+                                                        "pipeline_rows": stats["pipeline_rows"],
+                                                        "time_block": stats["time_block"]})
         adj_traffic = None
     fwd_roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": fwd_traffic, "kernel": fwd_name,
@@ -952,7 +984,8 @@ def main():
                    "snapshots": a.snapshot, "ckpt_stride": stats["ckpt_stride"],
                    "shot_wave": stats["shot_wave"], "shot_group": stats["shot_group"],
                    "tile_z": stats["tile_z"], "pipeline_forward": stats["pipeline_forward"],
-                   "pipeline_adjoint": stats["pipeline_adjoint"], "cuda_graph": not is3d,
+                   "pipeline_adjoint": stats["pipeline_adjoint"], "time_block": stats["time_block"],
+                   "cuda_graph": not is3d,
                    "autotuned": (not a.fixed) and not is3d,
                    "l2": (f"inputs larger than L2: {wl.ns} shots x {2 + 2 * ntr} field planes x "
                           f"{wl.cells_padded() * 4 / 1e6:.2f} MB = {live_mb:.0f} MB live state per step "
@@ -981,9 +1014,11 @@ def main():
     if precond is not None:
         line["precond"] = precond
     if is3d:  # the 2D kernel choices do not apply
-        for k in ("tile_z", "pipeline_forward", "pipeline_adjoint"):
+        for k in ("tile_z", "pipeline_forward", "pipeline_adjoint", "time_block"):
             line["config"].pop(k, None)
-        line["config"]["kernels"] = "k_fwd3d_cl (fused forward), k_step3d_ws<INC> (recompute), k_adj3d_cl (adjoint)"
+        line["config"]["kernels"] = ("k_step3d_ws<INC> + k_step3d_ws<BORN> (forward), k_step3d_ws<INC> (recompute), "
+                                     "k_step3d<ADJ> into checkpoint-segment images + k_kahan_fold (adjoint)"
+                                     if cl == 0 else f"cluster kernels (PROBE_OPT_CLUSTER3D = {cl})")
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -129,6 +129,11 @@ typedef enum {
                                     forward and adjoint */
     PROBE_OPT_PIPELINE_ADJ = 11, /* 2D adjoint kernel only (0, 2 or 3; PROBE_OPT_PIPELINE sets both) */
     PROBE_OPT_PIPE_ROWS_ADJ = 12, /* 2D pipelined adjoint only: rows per thread (1 or 2) */
+    PROBE_OPT_TBLOCK = 14,       /* 2D Born forward and checkpoint recompute: time levels advanced per
+                                    launch, 1 or 2 (two levels: each CTA stages its tile with an 8-cell
+                                    halo and recomputes the first level on the tile plus 4 cells, which
+                                    halves the state traffic per level); 0 (default) = chosen by the
+                                    autotuner.  Both give the same bits. */
     PROBE_OPT_CLUSTER3D = 13     /* 3D thread-block-cluster kernels, a bit mask (default 0):
                                     bit 0 (1): the incident and Born fields of a column tile advance in
                                     one launch on a cluster of 1 + nb CTAs (nb <= 7), exchanging Dtt u0
@@ -165,6 +170,7 @@ typedef struct {
     int dtt_history;             /* 1 when Dtt u^n of every step was kept instead of recomputed */
     int pipeline_rows;           /* rows per thread of the pipelined forward kernels (0: not pipelined) */
     int pipeline_rows_adjoint;   /* rows per thread of the pipelined adjoint kernel */
+    int time_block;              /* 2D Born forward and recompute: time levels per launch (1 or 2) */
 } probe_stats;
 
 /* Create a handle for one background model and acquisition geometry.

@@ -228,15 +228,19 @@ cudaError_t launch_check_finite(const float* a, long long n, int* err, cudaStrea
 // single BF16 position plane the imaging result is off by about 1e-2; the
 // two-term position plane (16 significant bits) leaves the rounding of q1,
 // which is 10-20 times smaller in absolute size, as the dominant term.
+struct CkptPlanes {
+    int pps, p_un, p_prev;  // planes per shot; planes of u^n and u^{n-1} within a shot's block
+};
+
 __device__ __forceinline__ float ckpt_value(const float* __restrict__ state, long long F, int plane,
-                                            int pc, long long i) {
+                                            CkptPlanes q, long long i) {
     const int shot = plane >> 1;
-    const float un = state[(long long)(2 * shot + pc) * F + i];
+    const float un = state[(long long)(q.pps * shot + q.p_un) * F + i];
     if ((plane & 1) == 0) return un;
-    return un - state[(long long)(2 * shot + (pc ^ 1)) * F + i];
+    return un - state[(long long)(q.pps * shot + q.p_prev) * F + i];
 }
 
-__global__ void k_absmax(const float* __restrict__ state, long long F, int pc, float* absmax) {
+__global__ void k_absmax(const float* __restrict__ state, long long F, CkptPlanes pc, float* absmax) {
     const int plane = blockIdx.y;
     float m = 0.f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < F;
@@ -267,7 +271,7 @@ size_t ckpt_bytes_per_shot(int dtype, long long F) {
 }
 
 // blockIdx.y = logical plane (2 j + 0: q0 of shot j, 2 j + 1: q1).
-__global__ void k_encode(const float* __restrict__ state, long long F, int pc, void* dst,
+__global__ void k_encode(const float* __restrict__ state, long long F, CkptPlanes pc, void* dst,
                          const float* __restrict__ absmax, float* scales, int dtype) {
     const int plane = blockIdx.y;
     const int shot = plane >> 1, which = plane & 1;
@@ -293,9 +297,9 @@ __global__ void k_encode(const float* __restrict__ state, long long F, int pc, v
     }
 }
 
-// blockIdx.y = shot: restores u^n into plane 2j + pc and u^{n-1} into 2j + (1 - pc).
+// blockIdx.y = shot: restores u^n and u^{n-1} into the shot's planes p_un and p_prev.
 __global__ void k_decode(const void* src, const float* __restrict__ scales, long long F, int dtype,
-                         int pc, float* __restrict__ state) {
+                         CkptPlanes pc, float* __restrict__ state) {
     const int shot = blockIdx.y;
     const float s0 = scales[2 * shot], s1 = scales[2 * shot + 1];
     const long long base = (long long)shot * ckpt_store_planes(dtype) * F;
@@ -313,16 +317,36 @@ __global__ void k_decode(const void* src, const float* __restrict__ scales, long
         }
         const float un = __fmul_rn(q0, s0);
         const float du = __fmul_rn(q1, s1);
-        state[(long long)(2 * shot + pc) * F + i] = un;
-        state[(long long)(2 * shot + (pc ^ 1)) * F + i] = __fsub_rn(un, du);
+        state[(long long)(pc.pps * shot + pc.p_un) * F + i] = un;
+        state[(long long)(pc.pps * shot + pc.p_prev) * F + i] = __fsub_rn(un, du);
     }
 }
 
-cudaError_t launch_encode_ckpt(const float* state, int nplanes, long long F, int pc, void* dst,
+// FP32 checkpoints: (u^n, u^{n-1}) of each shot copied as they are, u^n first.
+__global__ void k_copy_pair(const float* __restrict__ state, long long F, CkptPlanes q, float* __restrict__ dst,
+                            int to_state) {
+    const int plane = blockIdx.y;  // 2 shot + (0: u^n, 1: u^{n-1})
+    const int shot = plane >> 1;
+    const long long sp = (long long)(q.pps * shot + ((plane & 1) ? q.p_prev : q.p_un)) * F;
+    const long long cp = (long long)plane * F;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < F;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (to_state)
+            const_cast<float*>(state)[sp + i] = dst[cp + i];
+        else
+            dst[cp + i] = state[sp + i];
+    }
+}
+
+cudaError_t launch_encode_ckpt(const float* state, int nplanes, long long F, int pps, int p_un, int p_prev, void* dst,
                                float* scales, int dtype, float* absmax_scratch, cudaStream_t st) {
-    if (dtype == PROBE_SNAP_FP32)
-        return cudaMemcpyAsync(dst, state, (size_t)nplanes * F * sizeof(float),
-                               cudaMemcpyDeviceToDevice, st);
+    const CkptPlanes pc{pps, p_un, p_prev};
+    if (dtype == PROBE_SNAP_FP32) {
+        if (pps == 2 && p_un == 0 && p_prev == 1)  // already in checkpoint order
+            return cudaMemcpyAsync(dst, state, (size_t)nplanes * F * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        k_copy_pair<<<dim3(grid_for(F, 256, 64), nplanes), 256, 0, st>>>(state, F, pc, (float*)dst, 0);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaMemsetAsync(absmax_scratch, 0, nplanes * sizeof(float), st);
     if (e != cudaSuccess) return e;
     const int bx = grid_for(F, 256, 64);
@@ -331,11 +355,15 @@ cudaError_t launch_encode_ckpt(const float* state, int nplanes, long long F, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_decode_ckpt(const void* src, const float* scales, int nplanes, long long F,
-                               int pc, int dtype, float* state, cudaStream_t st) {
-    if (dtype == PROBE_SNAP_FP32)
-        return cudaMemcpyAsync(state, src, (size_t)nplanes * F * sizeof(float),
-                               cudaMemcpyDeviceToDevice, st);
+cudaError_t launch_decode_ckpt(const void* src, const float* scales, int nplanes, long long F, int pps, int p_un,
+                               int p_prev, int dtype, float* state, cudaStream_t st) {
+    const CkptPlanes pc{pps, p_un, p_prev};
+    if (dtype == PROBE_SNAP_FP32) {
+        if (pps == 2 && p_un == 0 && p_prev == 1)
+            return cudaMemcpyAsync(state, src, (size_t)nplanes * F * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        k_copy_pair<<<dim3(grid_for(F, 256, 64), nplanes), 256, 0, st>>>(state, F, pc, (float*)src, 1);
+        return cudaGetLastError();
+    }
     const int bx = grid_for(F, 256, 64);
     k_decode<<<dim3(bx, nplanes / 2), 256, 0, st>>>(src, scales, F, dtype, pc, state);
     return cudaGetLastError();

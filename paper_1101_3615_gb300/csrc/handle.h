@@ -26,6 +26,9 @@ struct Workspace {
     size_t bytes = 0;
     float* u = nullptr;       // [W][2][F]
     float* f = nullptr;       // [W][nb][2][F]
+    float* u4 = nullptr;      // 2D time-blocked forward: [W][4][F] (level n in plane n & 3)
+    float* f4 = nullptr;      // [W][nb][4][F]
+    CUtensorMap tm_u4h, tm_u4e, tm_f4h, tm_f4e, tm_dme;  // their boxes (80 x 32, 72 x 24) and dm's
     float* dm = nullptr;      // [nb][F]
     float* data = nullptr;    // [W][nb][nt][nr]
     void* ckpt = nullptr;     // [nck][W][2][F] (fp32 or 16-bit)
@@ -49,7 +52,7 @@ struct Workspace {
 // A captured sweep (forward + adjoint of one wave) and the key it was captured for.
 struct TunedEntry {
     std::vector<long long> key;  // kind, adjoint, then shots and trials of each model (and handles for groups)
-    int pipe_fwd = 2, pipe_adj = 2, group = 4, rows = 2, rows_adj = 1;
+    int pipe_fwd = 2, pipe_adj = 2, group = 4, rows = 2, rows_adj = 1, tblock = 1;
 };
 
 struct GraphEntry {
@@ -109,6 +112,8 @@ struct probe_s {
     int opt_timing = 0, opt_tile_z = 0, opt_pipeline = 2, opt_dtt_history = 0;
     int opt_autotune = 1;        // time the kernel variants on first use of a shape
     int opt_cluster3d = 0;       // 3D cluster kernels: bit 0 fused forward, bit 1 shot-clustered adjoint
+    int opt_tblock = 1;          // 2D Born forward and recompute: time levels per launch (1 or 2)
+    int user_tblock = 0;         // the caller fixed opt_tblock (else the autotuner chooses)
     int pipe_adj = 2;            // adjoint kernel variant (the forward uses opt_pipeline)
     int user_fixed = 0;          // the caller chose pipeline / shot group: no autotuning
     std::vector<probe::TunedEntry> tuned;  // autotuner results by workload key

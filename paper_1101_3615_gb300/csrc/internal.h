@@ -39,6 +39,11 @@ struct alignas(128) ModelStep2D {
     CUtensorMap tm_dtp;  // Dtt segment buffer, W * dtt_slots planes, plain box
     CUtensorMap tm_img;  // images [groups][nb] planes, plain box (pipelined adjoint)
     CUtensorMap tm_cmp;  // their Kahan compensation
+    // two-step (time-blocked) forward kernels over the four-level states u4 / f4: boxes of the tile
+    // plus an 8-cell halo (80 x 32) and of the first step's region, tile plus 4 (72 x 24)
+    CUtensorMap tm_u4h, tm_u4e, tm_f4h, tm_f4e;
+    CUtensorMap tm_se;   // s, 72 x 24 box
+    CUtensorMap tm_dme;  // dm, 72 x 24 box
     int Nz, Nx, P, pad, nz, nx;
     int tiles_x, tiles_z, ntiles;
     int ws_rows;                 // pipelined kernels: rows per thread R (tile height 16R)
@@ -73,6 +78,8 @@ struct alignas(128) ModelStep2D {
     long long F;       // floats per plane (Nz * P)
     float* u;          // incident state base
     float* f;          // Born/adjoint state base
+    float* u4;         // time-blocked forward: incident levels [W][4][F], level n in plane n & 3
+    float* f4;         // and Born levels [W][nb][4][F]
     const float* s;    // dt^2 / m on the padded grid [F]
     const float* dm;   // [nb][F] model perturbations (zero in the pad)
     float* dtt;        // segment buffer, Dtt u^n  [W][K][F]
@@ -94,6 +101,7 @@ struct StepParams2D {
     int nmodels;
     int total_items;  // pipelined kernels: work items over all models
     int n;    // time index of the step (forward: u^n -> u^{n+1}; adjoint: computes mu^n)
+    int two;  // time-blocked forward kernel: 1 = advance n -> n + 2, 0 = one step
     int nt;
     int* err; // device error word
     ModelStep2D m[kMaxModels];
@@ -167,6 +175,9 @@ cudaError_t launch_fwd2d(FwdKind kind, int tile_z, const StepParams2D& p, int bl
 cudaError_t launch_adj2d(int tile_z, int nbc, bool kahan, const StepParams2D& p, int blocks,
                          int chunks, cudaStream_t st);
 size_t fwd2d_smem_bytes(FwdKind kind, int tile_z);
+// Time-blocked forward (two levels per launch, one 64 x 16 tile per CTA) over u4 / f4: kind
+// FWD_BORN or FWD_INCIDENT_DTT; p.two selects two steps (n -> n + 2) or one.
+cudaError_t launch_fwd2d_tb(FwdKind kind, const StepParams2D& p, int blocks, cudaStream_t st);
 // Pipelined persistent variants (stencil2d_pipe.cu): tiles of 64 x 16R (R = m[].ws_rows, 1 or 2),
 // `stages`-deep TMA ring.  They need the handle's plain tile height kPipeTZ for its receiver lists.
 constexpr int kPipeTZ = 16;
@@ -198,11 +209,13 @@ cudaError_t launch_build_injection(const float* rdata, long long dss, long long 
                                    const int* uc_pos, float* inj, long long block, cudaStream_t st);
 // Checkpoint storage of one shot (FP32: 2 planes; FP16: 2 half planes; BF16: 3 bf16 planes).
 size_t ckpt_bytes_per_shot(int dtype, long long F);
-// pc = plane parity of u^n (u^{n-1} is in the other plane of each shot).
-cudaError_t launch_encode_ckpt(const float* state, int nplanes, long long F, int pc, void* dst,
+// State planes of shot j: pps planes per shot, u^n in plane pps j + p_un, u^{n-1} in pps j + p_prev
+// (the two-level states: pps = 2, p_un = n & 1; the four-level states of the time-blocked forward:
+// pps = 4, p_un = n & 3).  nplanes = 2 x shots.
+cudaError_t launch_encode_ckpt(const float* state, int nplanes, long long F, int pps, int p_un, int p_prev, void* dst,
                                float* scales, int dtype, float* absmax_scratch, cudaStream_t st);
-cudaError_t launch_decode_ckpt(const void* src, const float* scales, int nplanes, long long F,
-                               int pc, int dtype, float* state, cudaStream_t st);
+cudaError_t launch_decode_ckpt(const void* src, const float* scales, int nplanes, long long F, int pps, int p_un,
+                               int p_prev, int dtype, float* state, cudaStream_t st);
 cudaError_t launch_scale_copy(const float* src, float* dst, long long n, float a, cudaStream_t st);
 // img, comp (+)= seg with Kahan compensation (n floats): the end of a checkpoint segment of the 3D
 // adjoint, whose steps summed their imaging terms into the plain FP32 segment image seg.

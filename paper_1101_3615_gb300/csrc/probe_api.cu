@@ -120,6 +120,21 @@ probe_status encode_planes(probe_t h, CUtensorMap* map, float* base, int planes,
     return PROBE_OK;
 }
 
+// 2D FP32 tensor map over `planes` planes with a bx x bz box (the time-blocked kernels' boxes).
+probe_status encode_box(probe_t h, CUtensorMap* map, const float* base, int planes, int bx, int bz) {
+    TRY(get_encoder(h));
+    cuuint32_t es[3] = {1, 1, 1};
+    cuuint64_t dims[3] = {(cuuint64_t)h->Nx, (cuuint64_t)h->Nz, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)h->P * 4, (cuuint64_t)h->F * 4};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)bz, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(h, PROBE_ERR_CUDA, "cuTensorMapEncodeTiled (box) failed (" + std::to_string((int)r) + ")");
+    return PROBE_OK;
+}
+
 // 2D FP32 tensor map over `planes` planes with a plain 64 x rows box (no halo).
 probe_status encode_plain(probe_t h, CUtensorMap* map, const float* base, int planes, int rows) {
     TRY(get_encoder(h));
@@ -141,7 +156,7 @@ std::atomic<long long> g_generation{0};
 
 void free_ws(Workspace& w) {
     void* ptrs[] = {w.u, w.f, w.dm, w.data, w.ckpt, w.scales, w.absmax, w.dtt, w.img, w.comp, w.s_tmp,
-                    w.src_wave, w.inj, w.seg};
+                    w.src_wave, w.inj, w.seg, w.u4, w.f4};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Workspace();
@@ -159,6 +174,7 @@ bool use_history(probe_t h, int with_ckpt) { return with_ckpt && h->opt_dtt_hist
 void ws_bytes(probe_t h, int nb, int with_ckpt, int with_data, double* per_shot, double* fixed) {
     const double F4 = (double)h->F * 4.0;
     double ps = 2 * F4 + 2.0 * nb * F4;
+    if (h->ndim == 2) ps += 4 * F4 + 4.0 * nb * F4;  // four-level states of the time-blocked forward
     if (use_history(h, with_ckpt))
         ps += (double)(h->nt - 1) * F4;
     else if (with_ckpt)
@@ -279,6 +295,16 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     if (h->ndim == 2) {
         TRY(encode_ws_maps(h, w.mf, h->ws_rows));
         TRY(encode_ws_maps(h, w.ma, h->ws_rows_adj));
+        // four-level states of the time-blocked forward (zero: levels -1 and 0 start at rest)
+        TRY(alloc((void**)&w.u4, (size_t)W * 4 * F * 4));
+        TRY(alloc((void**)&w.f4, (size_t)W * std::max(nb, 1) * 4 * F * 4));
+        CK(h, cudaMemset(w.u4, 0, (size_t)W * 4 * F * 4));
+        CK(h, cudaMemset(w.f4, 0, (size_t)W * std::max(nb, 1) * 4 * F * 4));
+        TRY(encode_box(h, &w.tm_u4h, w.u4, W * 4, kTX + 16, 32));
+        TRY(encode_box(h, &w.tm_u4e, w.u4, W * 4, kTX + 8, 24));
+        TRY(encode_box(h, &w.tm_f4h, w.f4, W * std::max(nb, 1) * 4, kTX + 16, 32));
+        TRY(encode_box(h, &w.tm_f4e, w.f4, W * std::max(nb, 1) * 4, kTX + 8, 24));
+        TRY(encode_box(h, &w.tm_dme, w.dm, std::max(nb, 1), kTX + 8, 24));
     }
     w.tm_tile_z = h->tile_z;
     return PROBE_OK;
@@ -426,6 +452,14 @@ void fill_model(const Job& jb, ModelStep2D& m, const WsMaps& maps, int* blocks_f
     m.nband = h->nband;
     m.inj_slot = 0;
     if (encode_plain(h, &m.tm_sp, jb.s, 1, 16 * R) != PROBE_OK) m.s = nullptr;
+    m.tm_u4h = w.tm_u4h;
+    m.tm_u4e = w.tm_u4e;
+    m.tm_f4h = w.tm_f4h;
+    m.tm_f4e = w.tm_f4e;
+    m.tm_dme = w.tm_dme;
+    if (w.u4 && encode_box(h, &m.tm_se, jb.s, 1, kTX + 8, 24) != PROBE_OK) m.s = nullptr;
+    m.u4 = w.u4;
+    m.f4 = w.f4;
     m.Nz = h->Nz;
     m.Nx = h->Nx;
     m.P = h->P;
@@ -491,6 +525,7 @@ struct Sweep {
     int pipeline = 0;      // forward: 0 one tile per CTA; 2..4 persistent pipelined kernels
     int pipeline_adj = 0;  // adjoint variant
     int inj_hi = -1;       // time level of injection slot 0 of the current segment (-1: slot 0)
+    int tb = 1;            // Born forward and recompute: time levels per launch (1 or 2)
     bool kahan = true;
     cudaStream_t st = nullptr;
     int nt = 0, K = 0, nck = 0;
@@ -513,6 +548,7 @@ probe_status prepare_sweep(Sweep& sw, probe_t h0, cudaStream_t st) {
     sw.tile_z = h0->tile_z;
     sw.pipeline = h0->opt_pipeline;
     sw.pipeline_adj = h0->pipe_adj;
+    sw.tb = (h0->ndim == 2 && h0->tile_z == kPipeTZ && h0->ws.u4) ? h0->opt_tblock : 1;
     sw.kahan = h0->kahan != 0;
     int maxnb = 1;
     std::vector<int> bf(sw.jobs.size()), ba(sw.jobs.size());
@@ -569,6 +605,24 @@ probe_status launch_fwd_step(Sweep& sw, FwdKind kind, int n, int slot) {
     return PROBE_OK;
 }
 
+// Kernel launches of one checkpoint store (encode) or restore: FP32 copies are a plain memory copy
+// when the state planes are already in checkpoint order (u^n first).
+int codec_launches(int snap, bool encode, int pps, int p_un) {
+    if (snap == PROBE_SNAP_FP32) return (pps == 2 && p_un == 0) ? 0 : 1;
+    return encode ? 2 : 1;
+}
+
+// Time-blocked forward launch: levels n -> n + 2 (two) or n -> n + 1, Dtt into slots slot, slot + 1.
+probe_status launch_fwd_tb(Sweep& sw, FwdKind kind, int n, bool two, int slot) {
+    set_grid(sw, false);
+    sw.p.n = n;
+    sw.p.two = two ? 1 : 0;
+    for (int k = 0; k < sw.p.nmodels; ++k) sw.p.m[k].dtt_slot = slot;
+    cudaError_t e = launch_fwd2d_tb(kind, sw.p, sw.blocks_fwd, sw.st);
+    if (e != cudaSuccess) return cuda_fail(sw.jobs[0].h, e, "time-blocked forward launch");
+    return PROBE_OK;
+}
+
 probe_status launch_adj_step(Sweep& sw, int n, int slot) {
     set_grid(sw, true);
     sw.pa.n = n;
@@ -597,7 +651,51 @@ void record(probe_t h, int idx, cudaStream_t st) {
 }
 
 // Forward sweep.  kind: FWD_BORN / FWD_INCIDENT / FWD_INCIDENT_SAMPLE.
+// Born forward with two time levels per launch over the four-level states (levels n, n - 1 read,
+// n + 1, n + 2 written); checkpoints are taken between launches, where (u^m, u^{m-1}) of every m
+// the launch reached are in the planes m & 3, (m - 1) & 3.
+probe_status run_forward_tb(Sweep& sw, bool ckpt) {
+    for (Job& jb : sw.jobs) {
+        Workspace& w = jb.h->ws;
+        CK(jb.h, cudaMemsetAsync(w.u4, 0, (size_t)jb.W * 4 * jb.h->F * 4, sw.st));
+        CK(jb.h, cudaMemsetAsync(w.f4, 0, (size_t)jb.W * jb.nb * 4 * jb.h->F * 4, sw.st));
+    }
+    const bool history = sw.jobs[0].h->ws.history != 0;
+    auto store_ckpt = [&](int n) -> probe_status {
+        if (!ckpt || history || n % sw.K) return PROBE_OK;
+        for (Job& jb : sw.jobs) {
+            Workspace& w = jb.h->ws;
+            const int k = n / sw.K;
+            const size_t per = (size_t)jb.W * ckpt_bytes_per_shot(jb.h->snap, jb.h->F);
+            cudaError_t e = launch_encode_ckpt(w.u4, jb.W * 2, jb.h->F, 4, n & 3, (n + 3) & 3, (char*)w.ckpt + k * per,
+                                               w.scales + (size_t)k * jb.W * 2, jb.h->snap, w.absmax, sw.st);
+            if (e != cudaSuccess) return cuda_fail(jb.h, e, "checkpoint store");
+            sw.launches_other += codec_launches(jb.h->snap, true, 4, n & 3);
+        }
+        return PROBE_OK;
+    };
+    for (int n = 0; n < sw.nt - 1;) {
+        const bool two = n + 2 <= sw.nt - 1;
+        TRY(store_ckpt(n));
+        TRY(launch_fwd_tb(sw, FWD_BORN, n, two, history ? n : 0));
+        sw.launches_fwd++;
+        if (two) TRY(store_ckpt(n + 1));
+        n += two ? 2 : 1;
+    }
+    const int plane = (sw.nt - 1) & 3;  // last time level at the receivers
+    for (Job& jb : sw.jobs) {
+        probe_t h = jb.h;
+        Workspace& w = h->ws;
+        cudaError_t e = launch_sample(w.f4, (long long)jb.nb * 4 * h->F, 4 * h->F, plane, h->F, jb.W, jb.nb, h->d_rec,
+                                      h->nr, h->P, h->ndim, h->Ny, jb.data, jb.dss, jb.dts, sw.nt - 1, sw.st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "receiver sampling");
+        sw.launches_other++;
+    }
+    return PROBE_OK;
+}
+
 probe_status run_forward(Sweep& sw, FwdKind kind, bool ckpt) {
+    if (sw.tb == 2 && kind == FWD_BORN) return run_forward_tb(sw, ckpt);
     for (Job& jb : sw.jobs) {
         Workspace& w = jb.h->ws;
         CK(jb.h, cudaMemsetAsync(w.u, 0, (size_t)jb.W * 2 * jb.h->F * 4, sw.st));
@@ -613,10 +711,10 @@ probe_status run_forward(Sweep& sw, FwdKind kind, bool ckpt) {
                 const int k = n / sw.K;
                 const size_t per = (size_t)jb.W * ckpt_bytes_per_shot(jb.h->snap, jb.h->F);
                 void* dst = (char*)w.ckpt + (size_t)k * per;
-                cudaError_t e = launch_encode_ckpt(w.u, jb.W * 2, jb.h->F, n & 1, dst,
+                cudaError_t e = launch_encode_ckpt(w.u, jb.W * 2, jb.h->F, 2, n & 1, (n & 1) ^ 1, dst,
                                                    w.scales + (size_t)k * jb.W * 2, jb.h->snap, w.absmax, sw.st);
                 if (e != cudaSuccess) return cuda_fail(jb.h, e, "checkpoint store");
-                sw.launches_other += (jb.h->snap == PROBE_SNAP_FP32) ? 0 : 2;
+                sw.launches_other += codec_launches(jb.h->snap, true, 2, n & 1);
             }
         }
         TRY(launch_fwd_step(sw, kind, n, history ? n : 0));
@@ -685,18 +783,31 @@ probe_status run_adjoint(Sweep& sw) {
         const int k1 = std::min(k0 + sw.K, sw.nt - 1);
         if (k0 >= k1) continue;
         record(h0, ev++, sw.st);
+        const bool tb = sw.tb == 2;  // recompute two levels per launch over the four-level state
         for (Job& jb : sw.jobs) {
             Workspace& w = jb.h->ws;
             const size_t per = (size_t)jb.W * ckpt_bytes_per_shot(jb.h->snap, jb.h->F);
             const void* src = (const char*)w.ckpt + (size_t)k * per;
-            cudaError_t e = launch_decode_ckpt(src, w.scales + (size_t)k * jb.W * 2, jb.W * 2, jb.h->F, k0 & 1,
-                                               jb.h->snap, w.u, sw.st);
+            cudaError_t e = tb ? launch_decode_ckpt(src, w.scales + (size_t)k * jb.W * 2, jb.W * 2, jb.h->F, 4, k0 & 3,
+                                                    (k0 + 3) & 3, jb.h->snap, w.u4, sw.st)
+                               : launch_decode_ckpt(src, w.scales + (size_t)k * jb.W * 2, jb.W * 2, jb.h->F, 2, k0 & 1,
+                                                    (k0 & 1) ^ 1, jb.h->snap, w.u, sw.st);
             if (e != cudaSuccess) return cuda_fail(jb.h, e, "checkpoint restore");
-            sw.launches_other += (jb.h->snap == PROBE_SNAP_FP32) ? 0 : 1;
+            sw.launches_other += tb ? codec_launches(jb.h->snap, false, 4, k0 & 3)
+                                    : codec_launches(jb.h->snap, false, 2, k0 & 1);
         }
-        for (int j = k0; j < k1; ++j) {
-            TRY(launch_fwd_step(sw, FWD_INCIDENT_DTT, j, j - k0));
-            sw.launches_rec++;
+        if (tb) {
+            for (int j = k0; j < k1;) {
+                const bool two = j + 2 <= k1;
+                TRY(launch_fwd_tb(sw, FWD_INCIDENT_DTT, j, two, j - k0));
+                sw.launches_rec++;
+                j += two ? 2 : 1;
+            }
+        } else {
+            for (int j = k0; j < k1; ++j) {
+                TRY(launch_fwd_step(sw, FWD_INCIDENT_DTT, j, j - k0));
+                sw.launches_rec++;
+            }
         }
         record(h0, ev++, sw.st);
         TRY(build_injection(sw, k1, k0 + 1));
@@ -819,10 +930,10 @@ probe_status run_forward3d(const Job& jb, FwdKind kind, bool ckpt, cudaStream_t 
             const int k = n / h->K;
             const size_t per = (size_t)jb.W * ckpt_bytes_per_shot(h->snap, h->F);
             void* dst = (char*)w.ckpt + (size_t)k * per;
-            cudaError_t e = launch_encode_ckpt(w.u, jb.W * 2, h->F, n & 1, dst, w.scales + (size_t)k * jb.W * 2,
-                                               h->snap, w.absmax, st);
+            cudaError_t e = launch_encode_ckpt(w.u, jb.W * 2, h->F, 2, n & 1, (n & 1) ^ 1, dst,
+                                               w.scales + (size_t)k * jb.W * 2, h->snap, w.absmax, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint store");
-            c.other += (h->snap == PROBE_SNAP_FP32) ? 0 : 2;
+            c.other += codec_launches(h->snap, true, 2, n & 1);
         }
         if (fused) {
             pf.n = n;
@@ -887,10 +998,10 @@ probe_status run_adjoint3d(const Job& jb, cudaStream_t st, Count3& c) {
         record(h, ev++, st);
         const size_t per = (size_t)jb.W * ckpt_bytes_per_shot(h->snap, h->F);
         const void* src = (const char*)w.ckpt + (size_t)k * per;
-        cudaError_t e = launch_decode_ckpt(src, w.scales + (size_t)k * jb.W * 2, jb.W * 2, h->F, k0 & 1, h->snap, w.u,
-                                           st);
+        cudaError_t e = launch_decode_ckpt(src, w.scales + (size_t)k * jb.W * 2, jb.W * 2, h->F, 2, k0 & 1,
+                                           (k0 & 1) ^ 1, h->snap, w.u, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint restore");
-        c.other += (h->snap == PROBE_SNAP_FP32) ? 0 : 1;
+        c.other += codec_launches(h->snap, false, 2, k0 & 1);
         for (int j = k0; j < k1; ++j) {
             pi.m.Dout = w.dtt + (long long)(j - k0) * h->F;
             TRY(launch3(h, STEP3_INC, pi, j, st, "recompute step launch"));
@@ -1265,6 +1376,11 @@ extern "C" probe_status probe_set_option(probe_t h, int key, long long v) {
             h->user_fixed = 1;
             return PROBE_OK;
         case PROBE_OPT_USE_GRAPH: h->opt_use_graph = v ? 1 : 0; return PROBE_OK;
+        case PROBE_OPT_TBLOCK:
+            if (v < 0 || v > 2) return fail(h, PROBE_ERR_ARG, "tblock must be 0, 1 or 2");
+            h->user_tblock = v > 0 ? 1 : 0;
+            h->opt_tblock = v > 0 ? (int)v : 1;
+            return PROBE_OK;
         case PROBE_OPT_CLUSTER3D:
             if (v < 0 || v > 3) return fail(h, PROBE_ERR_ARG, "cluster3d must be 0..3");
             h->opt_cluster3d = (int)v;
@@ -1400,6 +1516,7 @@ probe_status autotune_2d(probe_t h, const std::vector<long long>& key, std::vect
             h->pipe_adj = t.pipe_adj;
             h->ws_rows = t.rows;
             h->ws_rows_adj = t.rows_adj;
+            if (!h->user_tblock) h->opt_tblock = t.tblock;
             *group = t.group;
             return PROBE_OK;
         }
@@ -1421,27 +1538,42 @@ probe_status autotune_2d(probe_t h, const std::vector<long long>& key, std::vect
     int best_rows_adj = h->ws_rows_adj;
     // candidates are timed round-robin, three rounds, keeping each one's fastest round
     constexpr int kRounds = 3, kReps = 24;
+    int best_tb = h->opt_tblock;
     {
-        const int pipes[5] = {0, 2, 3, 2, 3}, rows[5] = {1, 1, 1, 2, 2};
-        float t[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+        // candidates 0-4: one level per launch (one tile per CTA; pipelined S x R); 5: two levels per
+        // launch (time-blocked, one tile per CTA), timed per level; the pipelined candidates also set
+        // the adjoint's rows per thread
+        const int pipes[6] = {0, 2, 3, 2, 3, 0}, rows[6] = {1, 1, 1, 2, 2, 1};
+        const int ncand = (kind == FWD_BORN && !h->user_tblock && h->ws.u4 && h->nt >= 4) ? 6 : 5;
+        float t[6] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
         for (int r = 0; r < kRounds && rc == PROBE_OK; ++r)
-            for (int c = 0; c < 5 && rc == PROBE_OK; ++c) {
+            for (int c = 0; c < ncand && rc == PROBE_OK; ++c) {
                 h->opt_pipeline = pipes[c];
                 h->ws_rows = rows[c];
                 Sweep sw;
                 float ms = 0.f;
                 if ((rc = sweep_for(1, &sw)) != PROBE_OK) break;
-                auto fwd = [&](int i) {
-                    const int n = i % (h->nt - 1);
-                    return launch_fwd_step(sw, kind, n, base[0].h->ws.history ? n : 0);
-                };
-                if ((rc = time_steps(h, st, &ms, fwd, kReps)) != PROBE_OK) break;
+                const bool hist = base[0].h->ws.history != 0;
+                if (c == 5) {  // two levels per launch: half the launches for the same levels
+                    auto fwd2 = [&](int i) {
+                        const int n = (2 * i) % (h->nt - 2);
+                        return launch_fwd_tb(sw, kind, n, true, hist ? n : 0);
+                    };
+                    if ((rc = time_steps(h, st, &ms, fwd2, kReps / 2)) != PROBE_OK) break;
+                } else {
+                    auto fwd = [&](int i) {
+                        const int n = i % (h->nt - 1);
+                        return launch_fwd_step(sw, kind, n, hist ? n : 0);
+                    };
+                    if ((rc = time_steps(h, st, &ms, fwd, kReps)) != PROBE_OK) break;
+                }
                 t[c] = std::min(t[c], ms);
             }
         if (rc == PROBE_OK) {
-            const int c = (int)(std::min_element(t, t + 5) - t);
-            best_fwd = pipes[c];
-            best_rows = rows[c];
+            const int c5 = (int)(std::min_element(t, t + 5) - t);  // best one-level variant
+            best_fwd = pipes[c5];
+            best_rows = rows[c5];
+            if (ncand == 6) best_tb = (t[5] < t[c5]) ? 2 : 1;
         }
     }
     if (rc == PROBE_OK && adjoint) {
@@ -1481,6 +1613,7 @@ probe_status autotune_2d(probe_t h, const std::vector<long long>& key, std::vect
     h->opt_timing = saved_timing;
     h->opt_pipeline = best_fwd;
     h->pipe_adj = best_adj;
+    if (!h->user_tblock) h->opt_tblock = best_tb;
     if (rc != PROBE_OK) return rc;
     *group = best_grp;
     TunedEntry t;
@@ -1490,6 +1623,7 @@ probe_status autotune_2d(probe_t h, const std::vector<long long>& key, std::vect
     t.group = best_grp;
     t.rows = best_rows;
     t.rows_adj = best_rows_adj;
+    t.tblock = h->opt_tblock;
     h->tuned.push_back(t);
     return PROBE_OK;
 }
@@ -1581,6 +1715,7 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
             h->stats.pipeline_adjoint = piped ? h->pipe_adj : 0;
             h->stats.pipeline_rows = piped ? h->ws_rows : 0;
             h->stats.pipeline_rows_adjoint = piped ? h->ws_rows_adj : 0;
+            h->stats.time_block = (h->ndim == 2 && h->tile_z == kPipeTZ && w.u4) ? h->opt_tblock : 1;
             if (need_ckpt) {
                 CK(h, cudaMemsetAsync(w.img, 0, (size_t)G * nbw * h->F * 4, st));
                 CK(h, cudaMemsetAsync(w.comp, 0, (size_t)G * nbw * h->F * 4, st));
@@ -1602,7 +1737,7 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
             sw.jobs.push_back(jb);
             const std::vector<long long> key = {(long long)op, (long long)kind, (long long)need_ckpt, Wv, nbw, j0,
                                                 (long long)(size_t)jb.data, (long long)(size_t)jb.rdata,
-                                                (long long)(size_t)jb.s, h->ws.generation, h->opt_pipeline, h->pipe_adj, h->ws_rows, h->ws_rows_adj, h->opt_timing,
+                                                (long long)(size_t)jb.s, h->ws.generation, h->opt_pipeline, h->pipe_adj, h->ws_rows, h->ws_rows_adj, h->opt_timing, h->opt_tblock,
                                                 jb.shot_group, h->tile_z, h->nt};
             long long cnt[4] = {0, 0, 0, 0};
             TRY(run_maybe_graph(h, key, st, cnt, [&](cudaStream_t ss) -> probe_status {
@@ -1634,13 +1769,20 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
         // (no cluster fusion) also write Dtt u^n (4 B) and read it and s once per trial (8 B).
         const bool hist = w.history != 0;
         const bool split3 = h->ndim == 3 && kind == FWD_BORN && !((h->opt_cluster3d & 1) && nbw + 1 <= 8);
-        h->stats.bytes_forward += cells * steps * Wv *
-                                  (16.0 + (kind == FWD_BORN ? 16.0 * nbw : 0.0) + (hist ? 4.0 : 0.0) +
-                                   (split3 ? 4.0 + 8.0 * nbw : 0.0));
+        // 2D with two levels per launch: per cell and level (10 + 10 nb) bytes for the Born
+        // forward (u^n, u^{n-1}, s, two writes, per trial likewise, every other level) and 14 bytes
+        // for the recompute (with its two Dtt writes)
+        const bool tb2 = h->ndim == 2 && h->opt_tblock == 2 && h->tile_z == kPipeTZ && w.u4;
+        if (tb2 && kind == FWD_BORN)
+            h->stats.bytes_forward += cells * steps * Wv * (10.0 + 10.0 * nbw + (hist ? 4.0 : 0.0));
+        else
+            h->stats.bytes_forward += cells * steps * Wv *
+                                      (16.0 + (kind == FWD_BORN ? 16.0 * nbw : 0.0) + (hist ? 4.0 : 0.0) +
+                                       (split3 ? 4.0 + 8.0 * nbw : 0.0));
         if (need_ckpt) {
             if (!hist) {
                 h->stats.cell_updates_recompute += cells * steps * Wv;
-                h->stats.bytes_recompute += cells * steps * Wv * 20.0;
+                h->stats.bytes_recompute += cells * steps * Wv * (tb2 ? 14.0 : 20.0);
             }
             h->stats.cell_updates_adjoint += cells * steps * Wv * nbw;
             // adjoint: per (shot, trial) mu^{n+1}, mu^{n+2}, write mu^n = 12 B; per shot Dtt 4 B;

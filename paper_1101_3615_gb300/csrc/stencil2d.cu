@@ -534,6 +534,237 @@ cudaError_t launch_adj2d(int tile_z, int nbc, bool kahan, const StepParams2D& p,
     return cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------------------------------------
+// Time-blocked forward step: two time levels per launch (n -> n + 2), one 64 x 16 tile per CTA.
+//
+// The second level of a 64 x 16 output tile depends on the first level on the tile plus the
+// Laplacian's radius-4 halo (the extended region E, 72 x 24), which depends on level n on the
+// tile plus an 8-cell halo (80 x 32).  A CTA stages u^n (80 x 32), u^{n-1}, s (E) by TMA, computes
+// u^{n+1} and Dtt u^n on all of E into shared memory (cells outside the padded grid are zero, the
+// Laplacian's zero extension), then u^{n+2} on the tile; per Born trial the same with du^n,
+// du^{n-1}, dm, using Dtt u^n on E and Dtt u^{n+1} on the tile.  The halo cells of E are
+// recomputed by the neighbouring CTAs: 1.69x the arithmetic of the first level for half the state
+// traffic -- per cell and two steps the kernel reads u^n, u^{n-1}, s and per trial du^n, du^{n-1},
+// dm, and writes u^{n+1}, u^{n+2} and per trial du^{n+1}, du^{n+2}: (20 + 20 nb) bytes instead of
+// the (32 + 32 nb) of two single steps.  The states hold four levels (level n in plane n & 3) so
+// that no launch overwrites a level that a neighbouring tile still reads.  Every cell update is
+// the one-step kernel's arithmetic (lap4, the explicit roundings of leapfrog, the same source and
+// sponge terms), so both give the same bits; the receivers sample du^n and du^{n+1}.
+// ---------------------------------------------------------------------------
+constexpr int kTbHX = kTX + 16;       // 80
+constexpr int kTbHZ = 16 + 16;        // 32
+constexpr int kTbEX = kTX + 8;        // 72
+constexpr int kTbEZ = 16 + 8;         // 24
+constexpr int kTbH = kTbHX * kTbHZ;   // 2560 floats
+constexpr int kTbE = kTbEX * kTbEZ;   // 1728 floats
+constexpr int kTbGroups = (kTbEX / 4) * kTbEZ;  // 432 groups of 4 cells in E
+constexpr unsigned kTbLoadBytes = (kTbH + 2 * kTbE) * 4u;
+
+size_t fwd2d_tb_smem_bytes() { return (size_t)(2 * kTbH + 7 * kTbE) * 4; }
+
+// One step of the incident field on 4 cells (z, x..x+3): returns u^{n+1} in o and Dtt u^n in d.
+__device__ __forceinline__ void tb_incident4(const ModelStep2D& M, const float4& c, float L[4], const float4& sv,
+                                             const float4& uo, int z, int x, bool store_ok, int sz, int sx, float fsrc,
+                                             float o[4], float d[4]) {
+    if (z == sz) add_lane(L, sx - x, fsrc);
+    const bool interior = (z >= M.pad) && (z < M.pad + M.nz) && (x >= M.pad) && (x + 3 < M.pad + M.nx);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float Fo = __fmul_rn(get(sv, j), L[j]);
+        d[j] = __fmul_rn(Fo, M.inv_dt2);
+        float G = 1.f, am = 1.f;
+        if (!interior) sponge_factors(M, z, x + j, G, am);
+        o[j] = (store_ok && x + j >= 0 && x + j < M.Nx) ? leapfrog(G, get(c, j), am, get(uo, j), Fo) : 0.f;
+    }
+}
+
+// One step of a Born field on 4 cells, given Dtt u^n of the cells.
+__device__ __forceinline__ void tb_born4(const ModelStep2D& M, const float4& c, const float L[4], const float4& sv,
+                                         const float4& fo, const float4& dv, const float d[4], int z, int x,
+                                         bool store_ok, float o[4]) {
+    const bool interior = (z >= M.pad) && (z < M.pad + M.nz) && (x >= M.pad) && (x + 3 < M.pad + M.nx);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float src = __fmaf_rn(-get(dv, j), d[j], L[j]);
+        float G = 1.f, am = 1.f;
+        if (!interior) sponge_factors(M, z, x + j, G, am);
+        o[j] = (store_ok && x + j >= 0 && x + j < M.Nx) ? leapfrog(G, get(c, j), am, get(fo, j), __fmul_rn(get(sv, j), src))
+                                                         : 0.f;
+    }
+}
+
+// Receivers of the tile from a staged field array whose tile origin sits at (off, off).
+template <int HX>
+__device__ __forceinline__ void tb_sample(const float* t, int off, const ModelStep2D& M, int tile, int z0, int x0,
+                                          float* out) {
+    const int beg = M.rec_tile_ptr[tile], end = M.rec_tile_ptr[tile + 1];
+    for (int i = beg + (int)threadIdx.x; i < end; i += kThreads) {
+        const int r = M.rec_tile_idx[i];
+        out[r] = t[(M.rec_zx[2 * r] - z0 + off) * HX + (M.rec_zx[2 * r + 1] - x0 + off)];
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 3) k_fwd2d_tb(const __grid_constant__ StepParams2D p) {
+    constexpr bool BORN = (KIND == FWD_BORN);
+    constexpr bool DTT = (KIND == FWD_INCIDENT_DTT);
+    extern __shared__ __align__(128) float smem[];
+    float* U0 = smem;          // u^n, tile + 8
+    float* F0 = U0 + kTbH;     // du^n, tile + 8
+    float* U1 = F0 + kTbH;     // u^{n-1} on E
+    float* S = U1 + kTbE;      // s on E
+    float* UN = S + kTbE;      // u^{n+1} on E
+    float* DN = UN + kTbE;     // Dtt u^n on E
+    float* F1 = DN + kTbE;     // du^{n-1} on E
+    float* DM = F1 + kTbE;     // dm on E
+    float* FN = DM + kTbE;     // du^{n+1} on E
+    __shared__ __align__(8) uint64_t bars[2];
+
+    const int mi = find_model(p, blockIdx.z);
+    const ModelStep2D& M = p.m[mi];
+    if ((int)blockIdx.x >= M.tiles_x || (int)blockIdx.y >= M.tiles_z) return;
+    const int shot = blockIdx.z - M.block_begin;
+    const int tile = blockIdx.y * M.tiles_x + blockIdx.x;
+    const int z0 = blockIdx.y * 16, x0 = blockIdx.x * kTX;
+    const int tid = threadIdx.x;
+    const int n = p.n;
+    const bool two = p.two != 0;
+    const int pn = n & 3, pm = (n + 3) & 3, p1 = (n + 1) & 3, p2 = (n + 2) & 3;
+    const long long F = M.F;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(&bars[0], kTbLoadBytes);
+        tma_load_3d(U0, &M.tm_u4h, x0 - 8, z0 - 8, shot * 4 + pn, &bars[0]);
+        tma_load_3d(U1, &M.tm_u4e, x0 - 4, z0 - 4, shot * 4 + pm, &bars[0]);
+        tma_load_3d(S, &M.tm_se, x0 - 4, z0 - 4, 0, &bars[0]);
+    }
+    const bool ok0 = mbar_wait_bounded(&bars[0], 0);
+    if (__syncthreads_or(!ok0)) {
+        const uint32_t par[1] = {0u};
+        abort_cta(p.err, bars, 1, par);
+        return;
+    }
+    const int sz = M.src_zx[2 * shot], sx = M.src_zx[2 * shot + 1];
+    const float fsrc0 = M.wavelet[n] * M.vol_inv;
+    const float fsrc1 = two ? M.wavelet[n + 1] * M.vol_inv : 0.f;
+
+    // ---- incident, first level on E
+    for (int g = tid; g < kTbGroups; g += kThreads) {
+        const int er = g / (kTbEX / 4), ec = (g - er * (kTbEX / 4)) * 4;
+        const int z = z0 - 4 + er, x = x0 - 4 + ec;
+        float L[4], o[4], d[4];
+        float4 c;
+        lap4<kTbHX>(U0, er + 4, ec + 4, M, c, L);
+        tb_incident4(M, c, L, ld4(S + er * kTbEX + ec), ld4(U1 + er * kTbEX + ec), z, x, z >= 0 && z < M.Nz, sz, sx,
+                     fsrc0, o, d);
+        st4(UN + er * kTbEX + ec, make_float4(o[0], o[1], o[2], o[3]));
+        st4(DN + er * kTbEX + ec, make_float4(d[0], d[1], d[2], d[3]));
+    }
+    __syncthreads();
+
+    // ---- incident, second level on the tile
+    const int lx = (tid & 15) << 2, lz = tid >> 4;
+    const int z = z0 + lz, x = x0 + lx;
+    const bool valid = (z < M.Nz) && (x < M.Nx);
+    const long long off = (long long)z * M.P + x;
+    const int te = (lz + 4) * kTbEX + lx + 4;  // this thread's cells in the E arrays
+    const int th = (lz + 8) * kTbHX + lx + 8;  // and in the tile + 8 arrays
+    const float4 sv = ld4(S + te);
+    float d1[4] = {0.f, 0.f, 0.f, 0.f};
+    float* u4 = M.u4 + (long long)(shot * 4) * F;
+    if (two) {
+        float L[4], o[4];
+        float4 c1;
+        lap4<kTbEX>(UN, lz + 4, lx + 4, M, c1, L);
+        tb_incident4(M, c1, L, sv, ld4(U0 + th), z, x, true, sz, sx, fsrc1, o, d1);
+        if (valid) {
+            st4(u4 + p1 * F + off, c1);
+            st4(u4 + p2 * F + off, make_float4(o[0], o[1], o[2], o[3]));
+        }
+    } else if (valid) {
+        st4(u4 + p1 * F + off, ld4(UN + te));
+    }
+    if ((DTT || (BORN && M.dtt_store)) && valid) {
+        float* dst = M.dtt + (long long)shot * M.dtt_shot_stride + off;
+        st4(dst + (long long)M.dtt_slot * F, ld4(DN + te));
+        if (two) st4(dst + (long long)(M.dtt_slot + 1) * F, make_float4(d1[0], d1[1], d1[2], d1[3]));
+    }
+    if (!BORN) return;
+
+    const int nb = M.nb;
+    for (int b = 0; b < nb; ++b) {
+        __syncthreads();  // the previous trial is done with F0, F1, DM, FN
+        if (tid == 0) {
+            mbar_expect_tx(&bars[1], kTbLoadBytes);
+            tma_load_3d(F0, &M.tm_f4h, x0 - 8, z0 - 8, (shot * nb + b) * 4 + pn, &bars[1]);
+            tma_load_3d(F1, &M.tm_f4e, x0 - 4, z0 - 4, (shot * nb + b) * 4 + pm, &bars[1]);
+            tma_load_3d(DM, &M.tm_dme, x0 - 4, z0 - 4, b, &bars[1]);
+        }
+        const bool ok = mbar_wait_bounded(&bars[1], (uint32_t)(b & 1));
+        if (__syncthreads_or(!ok)) {
+            const uint32_t par[1] = {(uint32_t)(b & 1)};
+            abort_cta(p.err, bars + 1, 1, par);
+            return;
+        }
+        float* dout = M.data + (long long)shot * M.data_shot_stride + (long long)b * M.data_trial_stride;
+        tb_sample<kTbHX>(F0, 8, M, tile, z0, x0, dout + (long long)n * M.nr);
+        for (int g = tid; g < kTbGroups; g += kThreads) {
+            const int er = g / (kTbEX / 4), ec = (g - er * (kTbEX / 4)) * 4;
+            const int zz = z0 - 4 + er, xx = x0 - 4 + ec;
+            float L[4], o[4];
+            float4 c;
+            lap4<kTbHX>(F0, er + 4, ec + 4, M, c, L);
+            const float4 dd = ld4(DN + er * kTbEX + ec);
+            const float dv4[4] = {dd.x, dd.y, dd.z, dd.w};
+            tb_born4(M, c, L, ld4(S + er * kTbEX + ec), ld4(F1 + er * kTbEX + ec), ld4(DM + er * kTbEX + ec), dv4,
+                     zz, xx, zz >= 0 && zz < M.Nz, o);
+            st4(FN + er * kTbEX + ec, make_float4(o[0], o[1], o[2], o[3]));
+        }
+        __syncthreads();
+        float* f4 = M.f4 + (long long)((shot * nb + b) * 4) * F;
+        if (two) {
+            tb_sample<kTbEX>(FN, 4, M, tile, z0, x0, dout + (long long)(n + 1) * M.nr);
+            float L[4], o[4];
+            float4 c1;
+            lap4<kTbEX>(FN, lz + 4, lx + 4, M, c1, L);
+            tb_born4(M, c1, L, sv, ld4(F0 + th), ld4(DM + te), d1, z, x, true, o);
+            if (valid) {
+                st4(f4 + p1 * F + off, c1);
+                st4(f4 + p2 * F + off, make_float4(o[0], o[1], o[2], o[3]));
+            }
+        } else if (valid) {
+            st4(f4 + p1 * F + off, ld4(FN + te));
+        }
+    }
+}
+
+cudaError_t launch_fwd2d_tb(FwdKind kind, const StepParams2D& p, int zblocks, cudaStream_t st) {
+    if (zblocks <= 0) return cudaSuccess;
+    const dim3 grid = grid2d(p, zblocks);
+    const size_t sm = fwd2d_tb_smem_bytes();
+    cudaError_t e;
+    switch (kind) {
+        case FWD_BORN:
+            e = cudaFuncSetAttribute(k_fwd2d_tb<FWD_BORN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            k_fwd2d_tb<FWD_BORN><<<grid, kThreads, sm, st>>>(p);
+            break;
+        case FWD_INCIDENT_DTT:
+            e = cudaFuncSetAttribute(k_fwd2d_tb<FWD_INCIDENT_DTT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            k_fwd2d_tb<FWD_INCIDENT_DTT><<<grid, kThreads, sm, st>>>(p);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t stencil2d_configure() { return cudaSuccess; }
 
 }  // namespace probe

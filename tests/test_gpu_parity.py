@@ -135,8 +135,10 @@ def test_hessian_ragged_grid_and_launch_shapes(cuda_device, ragged, opts):
 
 
 def test_kernel_variants_give_identical_bits(cuda_device, ragged):
-    """Every 2D kernel family and tile shape, and the Dtt history, evaluate the same
-    operations in the same order: F, F* and H agree bit for bit (same shot grouping)."""
+    """Every 2D kernel family and tile shape, the Dtt history, and two time levels per launch
+    (an odd number of steps and odd checkpoint segments, so single-level launches finish them)
+    evaluate the same operations in the same order: F, F* and H agree bit for bit (same shot
+    grouping)."""
     wl, _ = ragged
     y = dev(wl.trials)
     d0 = None
@@ -144,7 +146,9 @@ def test_kernel_variants_give_identical_bits(cuda_device, ragged):
     for opts in [{"pipeline": 0}, {"pipeline": 2, "pipe_rows": 1}, {"pipeline": 3, "pipe_rows": 2},
                  {"pipeline": 2, "pipe_rows": 2, "use_graph": 1}, {"pipeline": 3, "pipe_rows": 1, "dtt_history": 1},
                  {"pipeline": 2, "pipe_rows": 1, "pipe_rows_adj": 2},
-                 {"pipeline": 2, "pipeline_adj": 0, "pipe_rows": 2}]:
+                 {"pipeline": 2, "pipeline_adj": 0, "pipe_rows": 2},
+                 {"tblock": 2}, {"tblock": 2, "dtt_history": 1},
+                 {"tblock": 2, "pipeline": 3, "pipe_rows": 1, "use_graph": 1}]:
         p = make_probe(wl)
         p.set_option("shot_group", 2)
         for k, v in opts.items():
@@ -157,6 +161,25 @@ def test_kernel_variants_give_identical_bits(cuda_device, ragged):
     for opts, img, hy in outs[1:]:
         assert torch.equal(img, outs[0][1]), opts
         assert torch.equal(hy, outs[0][2]), opts
+
+
+@pytest.mark.parametrize("snap", ["fp32", "fp16", "bf16"])
+def test_time_blocked_checkpoints_give_identical_bits(cuda_device, ragged, snap):
+    """Checkpoints taken from the four-level states of the two-level forward and restored for
+    the two-level recompute hold the same values as with one level per launch."""
+    wl, ref = ragged
+    y = dev(wl.trials)
+    out = []
+    for tb in (1, 2):
+        p = make_probe(wl, snapshot_dtype=snap)
+        p.set_option("shot_group", 2)
+        p.set_option("tblock", tb)
+        out.append(p.apply_H(y))
+        assert p.stats()["time_block"] == tb
+    assert torch.equal(out[0], out[1])
+    if snap == "fp32":
+        for b in range(3):
+            assert rel(out[1][b].cpu().numpy(), ref[b]) < 1e-4
 
 
 @pytest.mark.parametrize("opts", [{}, {"use_graph": 1}, {"use_graph": 1, "dtt_history": 1}])
