@@ -258,9 +258,10 @@ def kernel_label(pipeline, adjoint, ndim=2, cluster=False, group=1, time_block=0
                      "summed in distributed shared memory before one Kahan update)" if adjoint else
                      "k_fwd3d_cl (incident + Born fields of a column tile on a cluster of 1 + p CTAs, "
                      "Dtt u0 exchanged in distributed shared memory)"), "stencil3d.cu")
-        return (("k_step3d<ADJ> (adjoint + imaging into checkpoint-segment images, Kahan fold per segment)"
+        ws = "k_step3d_ws" if pipeline else "k_step3d"
+        return ((f"{ws}<ADJ> (adjoint + imaging into checkpoint-segment images, Kahan fold per segment)"
                  if adjoint else
-                 "k_step3d_ws<BORN> / <INC> (3D forward steps, one field kind per launch)"), "stencil3d.cu")
+                 f"{ws}<BORN> / <INC> (3D forward steps, one field kind per launch)"), "stencil3d.cu")
     if pipeline:
         name = (f"k_adj2d_ws<nbc, kahan, S={pipeline}>" if adjoint else
                 f"k_fwd2d_ws<FWD_BORN, S={pipeline}> (fused incident + Born step, warp-specialised TMA ring)")
@@ -1016,8 +1017,10 @@ def main():
     if is3d:  # the 2D kernel choices do not apply
         for k in ("tile_z", "pipeline_forward", "pipeline_adjoint", "time_block"):
             line["config"].pop(k, None)
-        line["config"]["kernels"] = ("k_step3d_ws<INC> + k_step3d_ws<BORN> (forward), k_step3d_ws<INC> (recompute), "
-                                     "k_step3d<ADJ> into checkpoint-segment images + k_kahan_fold (adjoint)"
+        fk = "k_step3d_ws" if stats["pipeline_forward"] else "k_step3d"
+        ak = "k_step3d_ws" if stats["pipeline_adjoint"] else "k_step3d"
+        line["config"]["kernels"] = (f"{fk}<INC> + {fk}<BORN> (forward), {fk}<INC> (recompute), "
+                                     f"{ak}<ADJ> into checkpoint-segment images + k_kahan_fold (adjoint)"
                                      if cl == 0 else f"cluster kernels (PROBE_OPT_CLUSTER3D = {cl})")
     if rank == 0:
         print(json.dumps(line))

@@ -118,7 +118,9 @@ typedef enum {
     PROBE_OPT_PIPELINE = 7,      /* 2D: 0 = one tile per CTA; 2 or 3 = persistent warp-specialised
                                     CTAs with a 2- or 3-stage TMA ring (tiles 64 x 16R, see
                                     PROBE_OPT_PIPE_ROWS), for the forward and the adjoint.  Every
-                                    variant gives the same bits. */
+                                    variant gives the same bits.  3D: 0 = one-barrier-per-plane
+                                    kernels, 2 or 3 (default 2) = producer-warp kernels, for the
+                                    forward and the adjoint. */
     PROBE_OPT_DTT_HISTORY = 8,   /* 2D: 1 = keep Dtt u^n of every step in device memory instead of
                                     checkpointing and recomputing (FP32, W (nt-1) planes); 0 (default) */
     PROBE_OPT_AUTOTUNE = 9,      /* 1 (default): on the first call for a shape, time the 2D kernel variants
@@ -127,7 +129,11 @@ typedef enum {
                                     PROBE_OPT_SHOT_GROUP turns it off */
     PROBE_OPT_PIPE_ROWS = 10,    /* 2D pipelined kernels: rows per thread R, tile 64 x 16R (1 or 2),
                                     forward and adjoint */
-    PROBE_OPT_PIPELINE_ADJ = 11, /* 2D adjoint kernel only (0, 2 or 3; PROBE_OPT_PIPELINE sets both) */
+    PROBE_OPT_PIPELINE_ADJ = 11, /* adjoint kernel only (0, 2 or 3; PROBE_OPT_PIPELINE sets both).  3D: nonzero
+                                    (default) = producer-warp adjoint with the receiver injection
+                                    prebuilt per checkpoint segment, used when Kahan compensation
+                                    is per segment or off; takes effect for workspaces sized after
+                                    it is set */
     PROBE_OPT_PIPE_ROWS_ADJ = 12, /* 2D pipelined adjoint only: rows per thread (1 or 2) */
     PROBE_OPT_TBLOCK = 14,       /* 2D Born forward and checkpoint recompute: time levels advanced per
                                     launch, 1 or 2 (two levels: each CTA stages its tile with an 8-cell
@@ -165,8 +171,10 @@ typedef struct {
     int shot_group;              /* shots per CTA in the adjoint */
     int tile_z;                  /* 2D tile height used */
     int ckpt_stride;             /* checkpoint spacing used */
-    int pipeline_forward;        /* 2D forward kernel: 0 one tile per CTA, 2..4 pipeline stages */
-    int pipeline_adjoint;        /* 2D adjoint kernel: same encoding */
+    int pipeline_forward;        /* 2D forward kernel: 0 one tile per CTA, 2..4 pipeline stages;
+                                    3D: 1 producer-warp kernels, 0 otherwise */
+    int pipeline_adjoint;        /* 2D adjoint kernel: same encoding; 3D: 1 producer-warp adjoint
+                                    (receiver injection from a per-segment band buffer) */
     int dtt_history;             /* 1 when Dtt u^n of every step was kept instead of recomputed */
     int pipeline_rows;           /* rows per thread of the pipelined forward kernels (0: not pipelined) */
     int pipeline_rows_adjoint;   /* rows per thread of the pipelined adjoint kernel */

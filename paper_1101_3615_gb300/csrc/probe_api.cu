@@ -171,6 +171,10 @@ long long inj_block(probe_t h) { return (long long)h->nband * (h->ndim == 3 ? (l
 // Bytes per resident shot and fixed bytes of a job with nb trials.
 bool use_history(probe_t h, int with_ckpt) { return with_ckpt && h->opt_dtt_history && h->ndim == 2; }
 
+// 3D adjoint on the producer-warp kernel (receiver injection from a per-segment band buffer)
+// rather than the one-barrier-per-plane kernel or the shot-cluster kernel.
+bool adj3d_ws(probe_t h) { return h->ndim == 3 && h->pipe_adj != 0 && !(h->opt_cluster3d & 2); }
+
 void ws_bytes(probe_t h, int nb, int with_ckpt, int with_data, double* per_shot, double* fixed) {
     const double F4 = (double)h->F * 4.0;
     double ps = 2 * F4 + 2.0 * nb * F4;
@@ -182,8 +186,8 @@ void ws_bytes(probe_t h, int nb, int with_ckpt, int with_data, double* per_shot,
     if (with_data) ps += (double)nb * h->nt * h->nr * 4.0;
     if (h->ndim == 3 && with_ckpt) {
         ps += 2.0 * nb * F4;  // per-shot images + compensation
-        if (h->opt_cluster3d & 2) ps += (double)h->K * nb * inj_block(h) * 4.0;  // injection of one segment
-        else if (h->kahan) ps += (double)nb * F4;                                 // segment images
+        if ((h->opt_cluster3d & 2) || adj3d_ws(h)) ps += (double)h->K * nb * inj_block(h) * 4.0;  // injection of one segment
+        if (!(h->opt_cluster3d & 2) && h->kahan) ps += (double)nb * F4;                          // segment images
     }
     *per_shot = ps;
     *fixed = nb * F4 + 2.0 * F4 * nb + F4;  // dm, one image group, s_tmp
@@ -277,7 +281,7 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     }
     TRY(alloc((void**)&w.s_tmp, (size_t)F * 4));
     TRY(alloc((void**)&w.src_wave, (size_t)W * 3 * 4));
-    if (with_ckpt && h->nband > 0 && (h->ndim == 2 || (h->opt_cluster3d & 2)))  // one segment of adjoint injection
+    if (with_ckpt && h->nband > 0 && (h->ndim == 2 || (h->opt_cluster3d & 2) || adj3d_ws(h)))  // one segment of adjoint injection
         TRY(alloc((void**)&w.inj, (size_t)h->K * W * std::max(nb, 1) * inj_block(h) * 4));
     // field planes must read as zero outside what the kernels write
     CK(h, cudaMemset(w.u, 0, (size_t)W * 2 * F * 4));
@@ -983,11 +987,14 @@ probe_status run_adjoint3d(const Job& jb, cudaStream_t st, Count3& c) {
     // shot-cluster adjoint: images of shot groups summed in shared memory, receiver injection
     // prebuilt per segment for the planes that hold receivers
     const bool clustered = (h->opt_cluster3d & 2) != 0;
+    // producer-warp adjoint: needs the injection buffer wherever there are receivers (a workspace
+    // sized before the option was set has none; the one-barrier kernel then assembles it itself)
+    const bool ws = adj3d_ws(h) && (h->nband == 0 || w.inj != nullptr);
     const int G = pick_group(h, h->ws.W);
     const long long block = inj_block(h);
-    if (clustered) {
+    if (clustered || ws) {
         pa.m.rrow = (h->nband > 0) ? h->d_rrow : nullptr;
-        pa.m.inj = w.inj;
+        pa.m.inj = (h->nband > 0) ? w.inj : nullptr;
         pa.m.inj_block = block;
     }
     int ev = 2;
@@ -1008,7 +1015,7 @@ probe_status run_adjoint3d(const Job& jb, cudaStream_t st, Count3& c) {
             c.rec++;
         }
         record(h, ev++, st);
-        if (clustered && h->nband > 0) {  // R^T r^n of levels k1 .. k0 + 1, slot k1 - n
+        if ((clustered || ws) && h->nband > 0) {  // R^T r^n of levels k1 .. k0 + 1, slot k1 - n
             CK(h, cudaMemsetAsync(w.inj, 0, (size_t)(k1 - k0) * jb.W * jb.nb * block * 4, st));
             cudaError_t e = launch_build_injection(jb.rdata, jb.dss, jb.dts, h->nr, k1, k1 - k0, jb.W, jb.nb, h->nuc,
                                                    h->d_uc_ptr, h->d_uc_rec, h->d_uc_pos, w.inj, block, st);
@@ -1022,15 +1029,17 @@ probe_status run_adjoint3d(const Job& jb, cudaStream_t st, Count3& c) {
                 pa.m.inj_slot = k1 - n;
                 cudaError_t e = launch_adj3d_cluster(G, h->kahan != 0, pa, st);
                 if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step launch");
-            } else if (w.seg) {
-                // two-level imaging sum: plain FP32 within the segment, Kahan across segments
-                pa.n = n;
-                pa.m.img = w.seg;
-                pa.m.seg_first = (n == k1) ? 1 : 0;
-                cudaError_t e = launch_step3d(STEP3_ADJ, false, h->opt_pipeline != 0, pa, st);
-                if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step launch");
             } else {
-                TRY(launch3(h, STEP3_ADJ, pa, n, st, "adjoint step launch"));
+                // with Kahan compensation: two-level imaging sum, plain FP32 within the segment,
+                // Kahan across segments; without: plain FP32 into the image itself
+                pa.n = n;
+                pa.m.inj_slot = k1 - n;
+                if (w.seg) {
+                    pa.m.img = w.seg;
+                    pa.m.seg_first = (n == k1) ? 1 : 0;
+                }
+                cudaError_t e = launch_step3d(STEP3_ADJ, !w.seg && h->kahan != 0, ws, pa, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step launch");
             }
             c.adj++;
         }
@@ -1713,6 +1722,10 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
             const bool piped = h->ndim == 2 && h->tile_z == kPipeTZ;
             h->stats.pipeline_forward = piped ? h->opt_pipeline : 0;
             h->stats.pipeline_adjoint = piped ? h->pipe_adj : 0;
+            if (h->ndim == 3) {  // 1 = the producer-warp kernel of the sweep
+                h->stats.pipeline_forward = (h->opt_pipeline != 0 && !(h->opt_cluster3d & 1)) ? 1 : 0;
+                h->stats.pipeline_adjoint = (adj3d_ws(h) && (h->nband == 0 || w.inj)) ? 1 : 0;
+            }
             h->stats.pipeline_rows = piped ? h->ws_rows : 0;
             h->stats.pipeline_rows_adjoint = piped ? h->ws_rows_adj : 0;
             h->stats.time_block = (h->ndim == 2 && h->tile_z == kPipeTZ && w.u4) ? h->opt_tblock : 1;

@@ -92,7 +92,8 @@ __device__ __forceinline__ void cells3(const ModelStep3D& M, const float* smem, 
                                        int y, int z, long long off, int shot, int b, long long F, float* outv,
                                        const Pw3& cur_pw, const float4& Gc, const float4& Ac, int sz, int sy,
                                        int sx, float fsrc, bool inj, float4 injv,
-                                       float4* dtt_out = nullptr, float4* prod_out = nullptr) {
+                                       float4* dtt_out = nullptr, float4* prod_out = nullptr,
+                                       const float* injq = nullptr) {
     const float* cur = smem + slot_c * kPlane3;
     const float* rp = cur + (ly + 4) * kHX3 + lx + 4;
     const float4 a = ld4(rp - 4), c = ld4(rp), d = ld4(rp + 4);
@@ -160,6 +161,12 @@ __device__ __forceinline__ void cells3(const ModelStep3D& M, const float* smem, 
             src[1] = injv.y;
             src[2] = injv.z;
             src[3] = injv.w;
+        } else if (injq) {  // injection read at its use (receiver planes only: no register held over the taps)
+            const float4 q = ld4(injq);
+            src[0] = q.x;
+            src[1] = q.y;
+            src[2] = q.z;
+            src[3] = q.w;
         }
     }
     const bool zin = (z >= M.pad) && (z < M.pad + M.nz);
@@ -343,17 +350,23 @@ __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ 
 
 constexpr int kWs3Threads = kThreads + 32;  // eight consumer warps + one producer warp
 
-// Pipelined variant for the forward modes (incident, nonlinear sampling, Born): one producer warp
-// streams the halo'd planes into the ring (per-slot full / empty mbarriers, one arrival per
-// consumer warp on release), so the consumer warps never meet at a CTA-wide barrier inside the
-// plane loop; each releases the oldest plane of its window as soon as it is done with it.  The
-// per-cell arithmetic is cells3, identical to k_step3d.  Every wait is bounded.
+// Pipelined variant (incident, nonlinear sampling, Born, and the adjoint without per-step Kahan
+// compensation): one producer warp streams the halo'd planes into the ring (per-slot full /
+// empty mbarriers, one arrival per consumer warp on release), so the consumer warps never meet
+// at a CTA-wide barrier inside the plane loop; each releases the oldest plane of its window as
+// soon as it is done with it.  The adjoint's receiver injection R^T r^n comes from the
+// segment's prebuilt band buffer (one float4 per thread on the planes that hold receivers)
+// instead of being assembled in shared memory.  The per-cell arithmetic is cells3, identical to
+// k_step3d.  Every wait is bounded.
 template <int MODE>
 __global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_constant__ StepParams3D p) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[kRing], empty[kRing];
-    __shared__ int srec[kZC3D + 1];  // receiver CSR bounds of this column tile's planes
+    // receiver CSR bounds of this column tile's planes (sampling), or each plane's injection
+    // band, -1 without receivers (adjoint)
+    __shared__ int srec[kZC3D + 1];
     constexpr bool SAMPLE = (MODE == STEP3_BORN || MODE == STEP3_INC_SAMPLE);
+    constexpr bool ADJ = (MODE == STEP3_ADJ);
     const ModelStep3D& M = p.m;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // grid.x = (column tile, chunk) x field with the field fastest: the fields of one tile run as
@@ -368,7 +381,7 @@ __global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_const
     const int zend = min(z0 + M.ZC, M.Nz);
     const int shot = blockIdx.y;
     const int n = p.n;
-    const int pc = n & 1, po = pc ^ 1;
+    const int pc = ADJ ? ((n + 1) & 1) : (n & 1), po = pc ^ 1;
     const long long F = M.F;
     const int vol_cur = shot * M.nvol_shot + 2 * b + pc;
     float* outv = M.state + (long long)(shot * M.nvol_shot + 2 * b + po) * F;
@@ -383,6 +396,7 @@ __global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_const
         fence_mbar_init();
     }
     if (SAMPLE && tid <= nloc) srec[tid] = M.rec_ptr[(tyi * M.tiles_x + txi) * M.Nz + z0 + tid];
+    if (ADJ && tid < nloc) srec[tid] = (M.rrow && M.inj) ? M.rrow[z0 + tid] : -1;
     __syncthreads();
 
     if (warp == kThreads / 32) {  // ---------------- producer warp
@@ -446,9 +460,16 @@ __global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_const
                 }
             }
         }
+        // the receiver injection of this plane's cells (adjoint): band srec[iz] of the segment's
+        // buffer, one Ny x P plane per band
+        const float* injq = nullptr;
+        if (ADJ && srec[iz] >= 0)
+            injq = M.inj + ((long long)(M.inj_slot * M.nshots + shot) * M.nfield + b) * M.inj_block +
+                   (long long)srec[iz] * plane_stride + (long long)y * M.P + x;
         if (col_ok && z < M.Nz)
             cells3<MODE, false>(M, smem, slot_c, lx, ly, x, y, z, off0 + (long long)iz * plane_stride, shot, b, F,
-                                outv, cur_pw, Gc, Ac, sz, sy, sx, fsrc, false, make_float4(0.f, 0.f, 0.f, 0.f));
+                                outv, cur_pw, Gc, Ac, sz, sy, sx, fsrc, false, make_float4(0.f, 0.f, 0.f, 0.f),
+                                nullptr, nullptr, injq);
         __syncwarp();
         if (lane == 0) {  // this warp is done with plane k = iz (the bottom of its window)
             int sf = slot_c - 4;
@@ -463,9 +484,15 @@ __global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_const
         return true;
     };
 
+    if (ADJ) {  // one plane per iteration: fewer registers spilled with the adjoint's operands
+#pragma unroll 1
+        for (int iz = 0; iz < nloc; ++iz)
+            if (!plane(iz)) return;
+    } else {
 #pragma unroll 2
-    for (int iz = 0; iz < nloc; ++iz)
-        if (!plane(iz)) return;
+        for (int iz = 0; iz < nloc; ++iz)
+            if (!plane(iz)) return;
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -963,7 +990,10 @@ cudaError_t launch_step3d(int mode, bool kahan, bool pipelined, const StepParams
             case STEP3_INC: return launch3_ws<STEP3_INC>(p, grid, st);
             case STEP3_INC_SAMPLE: return launch3_ws<STEP3_INC_SAMPLE>(p, grid, st);
             case STEP3_BORN: return launch3_ws<STEP3_BORN>(p, grid, st);
-            default: break;  // the adjoint keeps the one-barrier-per-plane kernel
+            case STEP3_ADJ:  // the per-step Kahan adjoint keeps the one-barrier-per-plane kernel
+                if (!kahan) return launch3_ws<STEP3_ADJ>(p, grid, st);
+                break;
+            default: break;
         }
     }
     switch (mode) {

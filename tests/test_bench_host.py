@@ -31,6 +31,9 @@ def test_kernel_labels_name_the_source_files():
     assert bench.kernel_label(0, True)[1] == "stencil2d.cu"
     assert bench.kernel_label(0, False, ndim=3)[1] == "stencil3d.cu"
     assert "k_adj3d_cl<G=4" in bench.kernel_label(0, True, ndim=3, cluster=True, group=4)[0]
+    assert bench.kernel_label(1, True, ndim=3)[0].startswith("k_step3d_ws<ADJ>")
+    assert bench.kernel_label(0, True, ndim=3)[0].startswith("k_step3d<ADJ>")
+    assert bench.kernel_label(3, False, time_block=2)[0].startswith("k_fwd2d_tb")
     for args in ((3, False), (2, True), (0, False), (0, True)):
         name, src = bench.kernel_label(*args)
         assert os.path.exists(os.path.join(bench.ROOT, "paper_1101_3615_gb300", "csrc", src))

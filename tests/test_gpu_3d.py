@@ -59,8 +59,10 @@ def test_born_data_3d(cuda_device, small3d):
 
 
 def test_forward_kernels_3d_agree(cuda_device, small3d):
-    """The producer-warp pipelined 3D forward kernels and the one-barrier-per-plane kernels run the
-    same per-cell arithmetic: F and H agree bit for bit."""
+    """The producer-warp pipelined 3D kernels (forward, and the adjoint with its receiver injection
+    from the per-segment band buffer) and the one-barrier-per-plane kernels (injection assembled in
+    shared memory) run the same per-cell arithmetic: F and H agree bit for bit (no grid cell holds
+    more than two receivers here, so the injection sums cannot differ in order)."""
     wl, prob, born, hes = small3d
     y = dev(wl.trials)
     out = []
@@ -68,6 +70,9 @@ def test_forward_kernels_3d_agree(cuda_device, small3d):
         p = make_probe(wl)
         p.set_option("pipeline", pipe)
         out.append((p.apply_F(y), p.apply_H(y)))
+        st = p.stats()
+        assert st["pipeline_forward"] == (1 if pipe else 0)
+        assert st["pipeline_adjoint"] == (1 if pipe else 0)
     assert torch.equal(out[0][0], out[1][0])
     assert torch.equal(out[0][1], out[1][1])
     for b in range(2):
