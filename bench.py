@@ -249,7 +249,7 @@ def kernel_source_hash(name):
 
 def kernel_label(pipeline, adjoint, ndim=2, cluster=False, group=1, time_block=0):
     """Kernel name and source file of the forward / adjoint step variant the handle ran."""
-    if ndim == 2 and time_block and not adjoint:
+    if ndim == 2 and time_block > 1 and not adjoint:
         return ("k_fwd2d_tb<FWD_BORN> (incident + Born fields advanced two time levels per launch)",
                 "stencil2d.cu")
     if ndim == 3:
@@ -279,6 +279,9 @@ def ncu_traffic(kind, source, variant):
             d = json.load(f)
         e = d[kind]
         if e.get("source") != source or e.get("source_sha") != kernel_source_hash(source):
+            return None
+        # the headers the kernel is compiled with (wait and copy helpers) must be unchanged too
+        if any(kernel_source_hash(f) != h for f, h in e.get("deps", {}).items()):
             return None
         if any(variant.get(k) != v for k, v in e.get("variant", {}).items()):
             return None

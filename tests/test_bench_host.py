@@ -34,6 +34,7 @@ def test_kernel_labels_name_the_source_files():
     assert bench.kernel_label(1, True, ndim=3)[0].startswith("k_step3d_ws<ADJ>")
     assert bench.kernel_label(0, True, ndim=3)[0].startswith("k_step3d<ADJ>")
     assert bench.kernel_label(3, False, time_block=2)[0].startswith("k_fwd2d_tb")
+    assert bench.kernel_label(3, False, time_block=1)[0].startswith("k_fwd2d_ws")   # one level per launch
     for args in ((3, False), (2, True), (0, False), (0, True)):
         name, src = bench.kernel_label(*args)
         assert os.path.exists(os.path.join(bench.ROOT, "paper_1101_3615_gb300", "csrc", src))
@@ -48,5 +49,7 @@ def test_committed_traffic_is_keyed_by_source_and_variant():
     other = {k: (v + 1 if isinstance(v, int) else v) for k, v in e["variant"].items()}
     assert bench.ncu_traffic("fwd_born", e["source"], other) is None
     assert bench.ncu_traffic("fwd_born", "stencil2d.cu", dict(e["variant"])) is None
+    for f, h in e.get("deps", {}).items():
+        assert len(h) == 16 and os.path.exists(os.path.join(bench.ROOT, "paper_1101_3615_gb300", "csrc", f))
     assert abs(e["dram_bytes_read_per_launch"] + e["dram_bytes_write_per_launch"]
                - e["dram_bytes_per_launch"]) < 1.0
