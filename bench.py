@@ -65,6 +65,7 @@ def parse():
                     help="stop after the timed steps and print their line (no breakdown, e2e, dot test, plain, "
                          "precond or CPU legs): the command whose kernel launches an ncu launch list records")
     ap.add_argument("--tblock", type=int, default=0, help="2D: time levels per launch (1 or 2; 0: autotuned)")
+    ap.add_argument("--planes3d", type=int, default=0, help="3D: z planes per CTA (32, 64, 128; 0: autotuned)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-history", action="store_true",
                     help="skip the extra measurement with the full Dtt history resident")
@@ -123,6 +124,8 @@ def profile_run(a, wl):
         p.set_option("shot_group", a.shot_group)
     if a.tblock and len(wl.shape) == 2:
         p.set_option("tblock", a.tblock)
+    if a.planes3d and len(wl.shape) == 3:
+        p.set_option("planes3d", a.planes3d)
     dm = torch.tensor(wl.trials, device=dev)
     if a.profile == "fwd":
         run = lambda: p.apply_F(dm)
@@ -743,6 +746,8 @@ def main():
         p.set_option("shot_group", a.shot_group)
     if a.tblock and not is3d:
         p.set_option("tblock", a.tblock)
+    if a.planes3d and is3d:
+        p.set_option("planes3d", a.planes3d)
     dm = torch.tensor(wl.trials, device=dev)
     out = torch.empty_like(dm)
     stream = torch.cuda.current_stream(dev)
@@ -1025,6 +1030,7 @@ def main():
         line["config"]["kernels"] = (f"{fk}<INC> + {fk}<BORN> (forward), {fk}<INC> (recompute), "
                                      f"{ak}<ADJ> into checkpoint-segment images + k_kahan_fold (adjoint)"
                                      if cl == 0 else f"cluster kernels (PROBE_OPT_CLUSTER3D = {cl})")
+        line["config"]["planes_per_cta"] = stats["planes_3d"]
     if rank == 0:
         print(json.dumps(line))
     if dist:

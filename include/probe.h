@@ -140,6 +140,11 @@ typedef enum {
                                     halo and recomputes the first level on the tile plus 4 cells, which
                                     halves the state traffic per level); 0 (default) = chosen by the
                                     autotuner.  Both give the same bits. */
+    PROBE_OPT_PLANES3D = 15,     /* 3D: z planes one CTA marches through (32, 64 or 128; each CTA loads
+                                    8 halo planes besides them); 0 (default) = chosen by the autotuner,
+                                    which times the forward step kernels on the real workspace at each
+                                    value on the first call for a workload.  All values give the same
+                                    bits. */
     PROBE_OPT_CLUSTER3D = 13     /* 3D thread-block-cluster kernels, a bit mask (default 0):
                                     bit 0 (1): the incident and Born fields of a column tile advance in
                                     one launch on a cluster of 1 + nb CTAs (nb <= 7), exchanging Dtt u0
@@ -179,6 +184,7 @@ typedef struct {
     int pipeline_rows;           /* rows per thread of the pipelined forward kernels (0: not pipelined) */
     int pipeline_rows_adjoint;   /* rows per thread of the pipelined adjoint kernel */
     int time_block;              /* 2D Born forward and recompute: time levels per launch (1 or 2) */
+    int planes_3d;               /* 3D: z planes marched by one CTA (0 for 2D) */
 } probe_stats;
 
 /* Create a handle for one background model and acquisition geometry.

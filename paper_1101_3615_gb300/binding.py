@@ -23,7 +23,7 @@ SNAP = {"fp32": 0, "bf16": 1, "fp16": 2}
 SOLVE = {"gd": 0, "cg": 1}
 OPT = {"check_finite": 1, "shot_wave": 2, "shot_group": 3, "use_graph": 4, "timing": 5, "tile_z": 6,
        "pipeline": 7, "dtt_history": 8, "autotune": 9, "pipe_rows": 10, "pipeline_adj": 11, "pipe_rows_adj": 12,
-       "cluster3d": 13, "tblock": 14}
+       "cluster3d": 13, "tblock": 14, "planes3d": 15}
 
 
 class probe_grid(C.Structure):
@@ -48,7 +48,7 @@ class probe_stats(C.Structure):
                 ("shot_wave", C.c_int), ("shot_group", C.c_int), ("tile_z", C.c_int),
                 ("ckpt_stride", C.c_int), ("pipeline_forward", C.c_int),
                 ("pipeline_adjoint", C.c_int), ("dtt_history", C.c_int), ("pipeline_rows", C.c_int),
-                ("pipeline_rows_adjoint", C.c_int), ("time_block", C.c_int)]
+                ("pipeline_rows_adjoint", C.c_int), ("time_block", C.c_int), ("planes_3d", C.c_int)]
 
 
 class ProbeError(RuntimeError):

@@ -115,6 +115,9 @@ struct probe_s {
     int opt_tblock = 1;          // 2D Born forward and recompute: time levels per launch (1 or 2)
     int user_tblock = 0;         // the caller fixed opt_tblock (else the autotuner chooses)
     int pipe_adj = 2;            // adjoint kernel variant (the forward uses opt_pipeline)
+    int zc3d = probe::kZC3D;     // 3D: z planes marched by one CTA (32, 64 or 128)
+    int user_zc3d = 0;           // the caller fixed zc3d (else the autotuner chooses)
+    std::vector<std::pair<std::vector<long long>, int>> tuned_zc3d;  // 3D autotuner results by key
     int user_fixed = 0;          // the caller chose pipeline / shot group: no autotuning
     std::vector<probe::TunedEntry> tuned;  // autotuner results by workload key
     probe_stats stats{};

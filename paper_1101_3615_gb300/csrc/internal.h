@@ -19,7 +19,8 @@ constexpr int kTX = 64;        // 2D tile width (x), 16 float4 lanes
 constexpr int kThreads = 256;  // threads per stencil CTA
 constexpr int kMaxNbc = 8;     // trials per adjoint CTA (register accumulators)
 constexpr int kTY3D = 16;      // 3D tile height (y)
-constexpr int kZC3D = 64;      // 3D planes marched by one CTA
+constexpr int kZC3D = 64;      // 3D planes marched by one CTA (default; the autotuner may pick 32 or 128)
+constexpr int kZCMax3D = 128;  // most 3D planes one CTA may march (size of the per-plane tables)
 
 // ---------------------------------------------------------------------------
 // Kernel parameter block of one model inside a (possibly multi-model) launch.

@@ -843,8 +843,8 @@ void fill3d(const Job& jb, ModelStep3D& m) {
     m.nx = h->nx;
     m.tiles_x = h->tiles_x;
     m.tiles_y = h->tiles_y;
-    m.zchunks = h->tiles_z;
-    m.ZC = kZC3D;
+    m.zchunks = (h->Nz + h->zc3d - 1) / h->zc3d;
+    m.ZC = h->zc3d;
     m.nshots = jb.W;
     m.nr = h->nr;
     m.cz = h->cz;
@@ -887,6 +887,84 @@ probe_status launch3(probe_t h, int mode, StepParams3D& p, int n, cudaStream_t s
     p.n = n;
     cudaError_t e = launch_step3d(mode, h->kahan != 0, h->opt_pipeline != 0, p, st);
     if (e != cudaSuccess) return cuda_fail(h, e, what);
+    return PROBE_OK;
+}
+
+// 3D autotuner: the z planes one CTA marches (32, 64, 128), timed on the real workspace on the
+// first call for a workload key -- one incident and (for the Born forward) one Born launch per
+// candidate, round-robin over three rounds, keeping each candidate's fastest round.  The launches
+// write only the state planes and the Dtt plane, which the sweep clears or rewrites before it
+// reads them.  The choice changes only how the grid is cut into CTAs, never a result.
+probe_status autotune_3d(const Job& jb, FwdKind kind, cudaStream_t st) {
+    probe_t h = jb.h;
+    if (h->ndim != 3 || h->user_zc3d || h->opt_cluster3d) return PROBE_OK;
+    const std::vector<long long> key = {(long long)kind, jb.W, jb.nb};
+    for (const auto& t : h->tuned_zc3d)
+        if (t.first == key) {
+            h->zc3d = t.second;
+            return PROBE_OK;
+        }
+    if (!h->opt_autotune) return PROBE_OK;
+    Workspace& w = h->ws;
+    if (!w.dtt) return PROBE_OK;
+    const bool born = kind == FWD_BORN;
+    StepParams3D pi, pb;
+    fill3d(jb, pi.m);
+    pi.nt = h->nt;
+    pi.err = h->d_err;
+    pi.m.tm = w.tm_u;
+    pi.m.state = w.u;
+    pi.m.nfield = 1;
+    pi.m.nvol_shot = 2;
+    pi.m.Dout = w.dtt;
+    pi.m.Dout_shot_stride = dtt_stride3(h);
+    if (born) {
+        fill3d(jb, pb.m);
+        pb.nt = h->nt;
+        pb.err = h->d_err;
+        pb.m.tm = w.tm_f;
+        pb.m.state = w.f;
+        pb.m.nfield = jb.nb;
+        pb.m.nvol_shot = 2 * jb.nb;
+        pb.m.Din = w.dtt;
+        pb.m.Din_shot_stride = dtt_stride3(h);
+    }
+    static const int cand[3] = {32, 64, 128};
+    float best[3] = {1e30f, 1e30f, 1e30f};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    probe_status ps = PROBE_OK;
+    for (int round = 0; round < 3 && ps == PROBE_OK; ++round) {
+        for (int c = 0; c < 3 && ps == PROBE_OK; ++c) {
+            const int zc = cand[c];
+            pi.m.ZC = pb.m.ZC = zc;
+            pi.m.zchunks = pb.m.zchunks = (h->Nz + zc - 1) / zc;
+            cudaEventRecord(e0, st);
+            for (int n = 0; n < 2 && ps == PROBE_OK; ++n) {
+                ps = launch3(h, STEP3_INC, pi, n, st, "autotuner launch");
+                if (ps == PROBE_OK && born) ps = launch3(h, STEP3_BORN, pb, n, st, "autotuner launch");
+            }
+            cudaEventRecord(e1, st);
+            if (ps != PROBE_OK) break;
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                ps = cuda_fail(h, e, "autotuner timing");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best[c] = std::min(best[c], ms);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TRY(ps);
+    int bi = 1;  // the default (64) unless another candidate is faster
+    for (int c = 0; c < 3; ++c)
+        if (best[c] < best[bi]) bi = c;
+    h->zc3d = cand[bi];
+    h->tuned_zc3d.push_back({key, h->zc3d});
     return PROBE_OK;
 }
 
@@ -1390,6 +1468,12 @@ extern "C" probe_status probe_set_option(probe_t h, int key, long long v) {
             h->user_tblock = v > 0 ? 1 : 0;
             h->opt_tblock = v > 0 ? (int)v : 1;
             return PROBE_OK;
+        case PROBE_OPT_PLANES3D:
+            if (v != 0 && v != 32 && v != 64 && v != 128)
+                return fail(h, PROBE_ERR_ARG, "planes3d must be 0, 32, 64 or 128");
+            h->user_zc3d = v ? 1 : 0;
+            h->zc3d = v ? (int)v : kZC3D;
+            return PROBE_OK;
         case PROBE_OPT_CLUSTER3D:
             if (v < 0 || v > 3) return fail(h, PROBE_ERR_ARG, "cluster3d must be 0..3");
             h->opt_cluster3d = (int)v;
@@ -1722,6 +1806,8 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
             const bool piped = h->ndim == 2 && h->tile_z == kPipeTZ;
             h->stats.pipeline_forward = piped ? h->opt_pipeline : 0;
             h->stats.pipeline_adjoint = piped ? h->pipe_adj : 0;
+            if (h->ndim == 3) TRY(autotune_3d(jb, kind, st));
+            h->stats.planes_3d = (h->ndim == 3) ? h->zc3d : 0;
             if (h->ndim == 3) {  // 1 = the producer-warp kernel of the sweep
                 h->stats.pipeline_forward = (h->opt_pipeline != 0 && !(h->opt_cluster3d & 1)) ? 1 : 0;
                 h->stats.pipeline_adjoint = (adj3d_ws(h) && (h->nband == 0 || w.inj)) ? 1 : 0;

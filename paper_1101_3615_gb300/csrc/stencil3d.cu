@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_const
     __shared__ __align__(8) uint64_t full[kRing], empty[kRing];
     // receiver CSR bounds of this column tile's planes (sampling), or each plane's injection
     // band, -1 without receivers (adjoint)
-    __shared__ int srec[kZC3D + 1];
+    __shared__ int srec[kZCMax3D + 1];
     constexpr bool SAMPLE = (MODE == STEP3_BORN || MODE == STEP3_INC_SAMPLE);
     constexpr bool ADJ = (MODE == STEP3_ADJ);
     const ModelStep3D& M = p.m;
@@ -521,7 +521,7 @@ size_t fwd3d_cluster_smem_bytes() { return (size_t)kRing * kPlaneBytes3 + (size_
 __global__ void __launch_bounds__(kWs3Threads, 2) k_fwd3d_cl(const __grid_constant__ StepParams3D p) {
     extern __shared__ __align__(128) float smem[];  // [kRing][kPlane3] ring, then [kDslots][kTile3] Dtt
     __shared__ __align__(8) uint64_t full[kRing], empty[kRing], dfull[kDslots], dempty[kDslots];
-    __shared__ int srec[kZC3D + 1];
+    __shared__ int srec[kZCMax3D + 1];
     const int nb = p.m2.nfield;
     const int nf = nb + 1;
     const uint32_t rank = cluster_ctarank();  // == blockIdx.x % nf: the field of this CTA
@@ -745,7 +745,7 @@ __global__ void __launch_bounds__(kWs3Threads, AdjCl<G>::kMinBlocks) k_adj3d_cl(
     constexpr int R = AdjCl<G>::R;  // reduction slots per owner
     extern __shared__ __align__(128) float smem[];  // ring, then reduction planes [R][G - 1][kTile3]
     __shared__ __align__(8) uint64_t full[kRing], empty[kRing], rfull[R], wok[G][R];
-    __shared__ int sband[kZC3D];  // receiver plane (band) index of each plane of the chunk, -1 without
+    __shared__ int sband[kZCMax3D];  // receiver plane (band) index of each plane of the chunk, -1 without
     const ModelStep3D& M = p.m;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = (int)(blockIdx.x % M.nfield);

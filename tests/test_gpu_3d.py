@@ -79,6 +79,28 @@ def test_forward_kernels_3d_agree(cuda_device, small3d):
         assert rel(out[1][1][b].cpu().numpy(), hes[b]) < 1e-4
 
 
+def test_plane_chunks_3d_give_identical_bits(cuda_device, small3d):
+    """The z planes one CTA marches (32, 64, 128, or the autotuner's pick) only change how the
+    grid is cut into CTAs: F and H are the same bits for every choice (34 padded planes here, so
+    32 cuts the column in two)."""
+    wl, prob, born, hes = small3d
+    y = dev(wl.trials)
+    out = []
+    for zc in (32, 64, 128, 0):
+        p = make_probe(wl)
+        p.set_option("planes3d", zc)
+        out.append((p.apply_F(y), p.apply_H(y)))
+        got = p.stats()["planes_3d"]
+        assert got == zc if zc else got in (32, 64, 128)
+    for o in out[1:]:
+        assert torch.equal(out[0][0], o[0])
+        assert torch.equal(out[0][1], o[1])
+    p = make_probe(wl)
+    from paper_1101_3615_gb300.binding import ProbeError
+    with pytest.raises(ProbeError):
+        p.set_option("planes3d", 48)
+
+
 def test_cluster_kernels_3d(cuda_device, small3d):
     """Thread-block-cluster kernels against the one-field-per-CTA kernels: the fused incident +
     Born step gives the same Born data bit for bit (same per-cell arithmetic, Dtt u0 exchanged in
