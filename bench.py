@@ -261,7 +261,8 @@ def kernel_label(pipeline, adjoint, ndim=2, cluster=False, group=1, time_block=0
                      "summed in distributed shared memory before one Kahan update)" if adjoint else
                      "k_fwd3d_cl (incident + Born fields of a column tile on a cluster of 1 + p CTAs, "
                      "Dtt u0 exchanged in distributed shared memory)"), "stencil3d.cu")
-        ws = "k_step3d_ws" if pipeline else "k_step3d"
+        ws = ("k_step3d_ws" if pipeline == 2 else "k_step3d_ws[last-warp refill]" if pipeline == 3
+              else "k_step3d")
         return ((f"{ws}<ADJ> (adjoint + imaging into checkpoint-segment images, Kahan fold per segment)"
                  if adjoint else
                  f"{ws}<BORN> / <INC> (3D forward steps, one field kind per launch)"), "stencil3d.cu")
@@ -1025,8 +1026,8 @@ def main():
     if is3d:  # the 2D kernel choices do not apply
         for k in ("tile_z", "pipeline_forward", "pipeline_adjoint", "time_block"):
             line["config"].pop(k, None)
-        fk = "k_step3d_ws" if stats["pipeline_forward"] else "k_step3d"
-        ak = "k_step3d_ws" if stats["pipeline_adjoint"] else "k_step3d"
+        fk = kernel_label(stats["pipeline_forward"], False, 3)[0].split("<")[0]
+        ak = kernel_label(stats["pipeline_adjoint"], True, 3)[0].split("<")[0]
         line["config"]["kernels"] = (f"{fk}<INC> + {fk}<BORN> (forward), {fk}<INC> (recompute), "
                                      f"{ak}<ADJ> into checkpoint-segment images + k_kahan_fold (adjoint)"
                                      if cl == 0 else f"cluster kernels (PROBE_OPT_CLUSTER3D = {cl})")

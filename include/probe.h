@@ -119,8 +119,11 @@ typedef enum {
                                     CTAs with a 2- or 3-stage TMA ring (tiles 64 x 16R, see
                                     PROBE_OPT_PIPE_ROWS), for the forward and the adjoint.  Every
                                     variant gives the same bits.  3D: 0 = one-barrier-per-plane
-                                    kernels, 2 or 3 (default 2) = producer-warp kernels, for the
-                                    forward and the adjoint. */
+                                    kernels; 2 = pipelined kernels whose ring is refilled by a
+                                    producer warp; 3 = pipelined kernels whose ring slot is refilled
+                                    by the last compute warp done with it (no producer warp); by
+                                    default the 3D autotuner picks 2 or 3, for the forward and the
+                                    adjoint.  Setting it turns that choice off. */
     PROBE_OPT_DTT_HISTORY = 8,   /* 2D: 1 = keep Dtt u^n of every step in device memory instead of
                                     checkpointing and recomputing (FP32, W (nt-1) planes); 0 (default) */
     PROBE_OPT_AUTOTUNE = 9,      /* 1 (default): on the first call for a shape, time the 2D kernel variants
@@ -177,9 +180,11 @@ typedef struct {
     int tile_z;                  /* 2D tile height used */
     int ckpt_stride;             /* checkpoint spacing used */
     int pipeline_forward;        /* 2D forward kernel: 0 one tile per CTA, 2..4 pipeline stages;
-                                    3D: 1 producer-warp kernels, 0 otherwise */
-    int pipeline_adjoint;        /* 2D adjoint kernel: same encoding; 3D: 1 producer-warp adjoint
-                                    (receiver injection from a per-segment band buffer) */
+                                    3D: 0 one barrier per plane, 2 producer-warp refill, 3 refill by
+                                    the last compute warp */
+    int pipeline_adjoint;        /* 2D adjoint kernel: same encoding; 3D: as the forward, for the
+                                    adjoint with the receiver injection from a per-segment band
+                                    buffer */
     int dtt_history;             /* 1 when Dtt u^n of every step was kept instead of recomputed */
     int pipeline_rows;           /* rows per thread of the pipelined forward kernels (0: not pipelined) */
     int pipeline_rows_adjoint;   /* rows per thread of the pipelined adjoint kernel */

@@ -57,6 +57,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Shared-memory counter increment with acquire-release semantics at CTA scope: the caller's
+// earlier accesses are ordered before it, and the thread that reads the final count sees every
+// other incrementer's earlier accesses.  Returns the previous value.
+__device__ __forceinline__ uint32_t atom_add_acqrel_shared(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(p)), "r"(v)
+                 : "memory");
+    return old;
+}
+
+// Orders this thread's generic-proxy shared-memory accesses (and those it has observed) before
+// its subsequent async-proxy operations (a TMA write into a slot that was just read).
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Wait for phase `parity` of `bar`; false if it did not complete within `limit_ns`.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   unsigned long long limit_ns = kWaitLimitNs) {

@@ -55,6 +55,12 @@ struct TunedEntry {
     int pipe_fwd = 2, pipe_adj = 2, group = 4, rows = 2, rows_adj = 1, tblock = 1;
 };
 
+// 3D autotuner result: refill scheme of the pipelined forward and adjoint kernels, planes per CTA.
+struct Tuned3 {
+    std::vector<long long> key;  // kind, adjoint, shots, trials
+    int fam_fwd = 2, fam_adj = 2, zc = 64;
+};
+
 struct GraphEntry {
     std::vector<long long> key;
     cudaGraphExec_t exec = nullptr;
@@ -117,7 +123,7 @@ struct probe_s {
     int pipe_adj = 2;            // adjoint kernel variant (the forward uses opt_pipeline)
     int zc3d = probe::kZC3D;     // 3D: z planes marched by one CTA (32, 64 or 128)
     int user_zc3d = 0;           // the caller fixed zc3d (else the autotuner chooses)
-    std::vector<std::pair<std::vector<long long>, int>> tuned_zc3d;  // 3D autotuner results by key
+    std::vector<probe::Tuned3> tuned3;  // 3D autotuner results by workload key
     int user_fixed = 0;          // the caller chose pipeline / shot group: no autotuning
     std::vector<probe::TunedEntry> tuned;  // autotuner results by workload key
     probe_stats stats{};

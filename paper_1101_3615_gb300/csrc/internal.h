@@ -158,8 +158,8 @@ struct StepParams3D {
     ModelStep3D m2;  // cluster kernels: the Born fields of the fused forward step
 };
 
-// pipelined: the producer-warp variant for the forward modes (the adjoint always uses k_step3d)
-cudaError_t launch_step3d(int mode, bool kahan, bool pipelined, const StepParams3D& p, cudaStream_t st);
+// pipeline: 0 one barrier per plane; 2 producer warp; 3 the last compute warp out of a slot refills it
+cudaError_t launch_step3d(int mode, bool kahan, int pipeline, const StepParams3D& p, cudaStream_t st);
 size_t step3d_smem_bytes();
 // Fused incident + Born step on clusters of 1 + nb CTAs (m: incident, m2: Born, nb = m2.nfield <= 7).
 cudaError_t launch_fwd3d_cluster(const StepParams3D& p, cudaStream_t st);

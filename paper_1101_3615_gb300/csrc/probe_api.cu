@@ -885,30 +885,38 @@ struct Count3 {
 
 probe_status launch3(probe_t h, int mode, StepParams3D& p, int n, cudaStream_t st, const char* what) {
     p.n = n;
-    cudaError_t e = launch_step3d(mode, h->kahan != 0, h->opt_pipeline != 0, p, st);
+    cudaError_t e = launch_step3d(mode, h->kahan != 0, h->opt_pipeline, p, st);
     if (e != cudaSuccess) return cuda_fail(h, e, what);
     return PROBE_OK;
 }
 
-// 3D autotuner: the z planes one CTA marches (32, 64, 128), timed on the real workspace on the
-// first call for a workload key -- one incident and (for the Born forward) one Born launch per
-// candidate, round-robin over three rounds, keeping each candidate's fastest round.  The launches
-// write only the state planes and the Dtt plane, which the sweep clears or rewrites before it
-// reads them.  The choice changes only how the grid is cut into CTAs, never a result.
-probe_status autotune_3d(const Job& jb, FwdKind kind, cudaStream_t st) {
+// 3D autotuner, on the first call for a workload key, timed on the real workspace (round-robin
+// over three rounds, each candidate's fastest round kept): the z planes one CTA marches (32, 64,
+// 128) with the ring-refill scheme of the pipelined forward kernels (2: producer warp, 3: the
+// last compute warp out of a slot) on one incident and (for the Born forward) one Born launch per
+// candidate; then, for calls with an adjoint sweep, the refill scheme of the adjoint on one
+// adjoint launch per scheme.  The launches write only the state planes, the Dtt plane and the
+// segment image or the image, which the call clears or rewrites before it reads them.  None of
+// the choices changes a result.
+probe_status autotune_3d(const Job& jb, FwdKind kind, bool adjoint, cudaStream_t st) {
     probe_t h = jb.h;
-    if (h->ndim != 3 || h->user_zc3d || h->opt_cluster3d) return PROBE_OK;
-    const std::vector<long long> key = {(long long)kind, jb.W, jb.nb};
-    for (const auto& t : h->tuned_zc3d)
-        if (t.first == key) {
-            h->zc3d = t.second;
+    const bool fam_fixed = h->user_fixed || h->opt_pipeline == 0;
+    if (h->ndim != 3 || (h->user_zc3d && fam_fixed) || h->opt_cluster3d) return PROBE_OK;
+    const std::vector<long long> key = {(long long)kind, (long long)adjoint, jb.W, jb.nb};
+    for (const Tuned3& t : h->tuned3)
+        if (t.key == key) {
+            if (!h->user_zc3d) h->zc3d = t.zc;
+            if (!fam_fixed) {
+                h->opt_pipeline = t.fam_fwd;
+                h->pipe_adj = t.fam_adj;
+            }
             return PROBE_OK;
         }
     if (!h->opt_autotune) return PROBE_OK;
     Workspace& w = h->ws;
     if (!w.dtt) return PROBE_OK;
     const bool born = kind == FWD_BORN;
-    StepParams3D pi, pb;
+    StepParams3D pi, pb, pa;
     fill3d(jb, pi.m);
     pi.nt = h->nt;
     pi.err = h->d_err;
@@ -918,53 +926,101 @@ probe_status autotune_3d(const Job& jb, FwdKind kind, cudaStream_t st) {
     pi.m.nvol_shot = 2;
     pi.m.Dout = w.dtt;
     pi.m.Dout_shot_stride = dtt_stride3(h);
-    if (born) {
-        fill3d(jb, pb.m);
-        pb.nt = h->nt;
-        pb.err = h->d_err;
-        pb.m.tm = w.tm_f;
-        pb.m.state = w.f;
-        pb.m.nfield = jb.nb;
-        pb.m.nvol_shot = 2 * jb.nb;
-        pb.m.Din = w.dtt;
-        pb.m.Din_shot_stride = dtt_stride3(h);
+    fill3d(jb, pb.m);  // Born fields (forward) and adjoint fields share the f planes
+    pb.nt = h->nt;
+    pb.err = h->d_err;
+    pb.m.tm = w.tm_f;
+    pb.m.state = w.f;
+    pb.m.nfield = jb.nb;
+    pb.m.nvol_shot = 2 * jb.nb;
+    pb.m.Din = w.dtt;
+    pb.m.Din_shot_stride = dtt_stride3(h);
+    pa = pb;  // adjoint: no receiver injection (rrow null); a segment's first step writes its image
+    if (w.seg) {
+        pa.m.img = w.seg;
+        pa.m.seg_first = 1;
     }
-    static const int cand[3] = {32, 64, 128};
-    float best[3] = {1e30f, 1e30f, 1e30f};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
-    probe_status ps = PROBE_OK;
-    for (int round = 0; round < 3 && ps == PROBE_OK; ++round) {
-        for (int c = 0; c < 3 && ps == PROBE_OK; ++c) {
-            const int zc = cand[c];
-            pi.m.ZC = pb.m.ZC = zc;
-            pi.m.zchunks = pb.m.zchunks = (h->Nz + zc - 1) / zc;
-            cudaEventRecord(e0, st);
-            for (int n = 0; n < 2 && ps == PROBE_OK; ++n) {
-                ps = launch3(h, STEP3_INC, pi, n, st, "autotuner launch");
-                if (ps == PROBE_OK && born) ps = launch3(h, STEP3_BORN, pb, n, st, "autotuner launch");
-            }
-            cudaEventRecord(e1, st);
-            if (ps != PROBE_OK) break;
-            cudaError_t e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) {
-                ps = cuda_fail(h, e, "autotuner timing");
-                break;
-            }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            best[c] = std::min(best[c], ms);
+    // times `body` (which launches on st) and keeps the minimum in *best
+    auto timed = [&](float* best, auto body) -> probe_status {
+        cudaEventRecord(e0, st);
+        probe_status ps = body();
+        cudaEventRecord(e1, st);
+        if (ps != PROBE_OK) return ps;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) return cuda_fail(h, e, "autotuner timing");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *best = std::min(*best, ms);
+        return PROBE_OK;
+    };
+    auto set_zc = [&](int zc) {
+        for (StepParams3D* q : {&pi, &pb, &pa}) {
+            q->m.ZC = zc;
+            q->m.zchunks = (h->Nz + zc - 1) / zc;
         }
+    };
+    // forward: (refill scheme, planes); the caller's fixed choices stay fixed
+    std::vector<int> fams = {2, 3}, zcs = {32, 64, 128};
+    if (fam_fixed) fams = {h->opt_pipeline};
+    if (h->user_zc3d) zcs = {h->zc3d};
+    std::vector<std::pair<int, int>> cand;
+    for (int fam : fams)
+        for (int zc : zcs) cand.push_back({fam, zc});
+    const int nc = (int)cand.size();
+    std::vector<float> best(nc, 1e30f);
+    probe_status ps = PROBE_OK;
+    for (int round = 0; round < 3 && ps == PROBE_OK; ++round)
+        for (int c = 0; c < nc && ps == PROBE_OK; ++c) {
+            set_zc(cand[c].second);
+            ps = timed(&best[c], [&]() -> probe_status {
+                for (int n = 0; n < 2; ++n) {
+                    pi.n = pb.n = n;
+                    cudaError_t e = launch_step3d(STEP3_INC, false, cand[c].first, pi, st);
+                    if (e == cudaSuccess && born) e = launch_step3d(STEP3_BORN, false, cand[c].first, pb, st);
+                    if (e != cudaSuccess) return cuda_fail(h, e, "autotuner launch");
+                }
+                return PROBE_OK;
+            });
+        }
+    int bi = 0;
+    for (int c = 1; c < nc; ++c)
+        if (best[c] < best[bi]) bi = c;
+    const int zc = h->user_zc3d ? h->zc3d : cand[bi].second;
+    const int fam_fwd = cand[bi].first;
+    // adjoint refill scheme at the chosen planes
+    int fam_adj = fam_fixed ? h->pipe_adj : fam_fwd;
+    if (ps == PROBE_OK && adjoint && !fam_fixed && adj3d_ws(h)) {
+        float ba[2] = {1e30f, 1e30f};
+        set_zc(zc);
+        for (int round = 0; round < 3 && ps == PROBE_OK; ++round)
+            for (int c = 0; c < 2 && ps == PROBE_OK; ++c)
+                ps = timed(&ba[c], [&]() -> probe_status {
+                    for (int n = 0; n < 2; ++n) {
+                        pa.n = h->nt - 1 - n;
+                        cudaError_t e = launch_step3d(STEP3_ADJ, false, 2 + c, pa, st);
+                        if (e != cudaSuccess) return cuda_fail(h, e, "autotuner launch");
+                    }
+                    return PROBE_OK;
+                });
+        fam_adj = (ba[1] < ba[0]) ? 3 : 2;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     TRY(ps);
-    int bi = 1;  // the default (64) unless another candidate is faster
-    for (int c = 0; c < 3; ++c)
-        if (best[c] < best[bi]) bi = c;
-    h->zc3d = cand[bi];
-    h->tuned_zc3d.push_back({key, h->zc3d});
+    h->zc3d = zc;
+    if (!fam_fixed) {
+        h->opt_pipeline = fam_fwd;
+        h->pipe_adj = fam_adj;
+    }
+    Tuned3 t;
+    t.key = key;
+    t.fam_fwd = h->opt_pipeline;
+    t.fam_adj = h->pipe_adj;
+    t.zc = h->zc3d;
+    h->tuned3.push_back(t);
     return PROBE_OK;
 }
 
@@ -1116,7 +1172,7 @@ probe_status run_adjoint3d(const Job& jb, cudaStream_t st, Count3& c) {
                     pa.m.img = w.seg;
                     pa.m.seg_first = (n == k1) ? 1 : 0;
                 }
-                cudaError_t e = launch_step3d(STEP3_ADJ, !w.seg && h->kahan != 0, ws, pa, st);
+                cudaError_t e = launch_step3d(STEP3_ADJ, !w.seg && h->kahan != 0, ws ? h->pipe_adj : 0, pa, st);
                 if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step launch");
             }
             c.adj++;
@@ -1806,11 +1862,11 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
             const bool piped = h->ndim == 2 && h->tile_z == kPipeTZ;
             h->stats.pipeline_forward = piped ? h->opt_pipeline : 0;
             h->stats.pipeline_adjoint = piped ? h->pipe_adj : 0;
-            if (h->ndim == 3) TRY(autotune_3d(jb, kind, st));
+            if (h->ndim == 3) TRY(autotune_3d(jb, kind, need_ckpt, st));
             h->stats.planes_3d = (h->ndim == 3) ? h->zc3d : 0;
-            if (h->ndim == 3) {  // 1 = the producer-warp kernel of the sweep
-                h->stats.pipeline_forward = (h->opt_pipeline != 0 && !(h->opt_cluster3d & 1)) ? 1 : 0;
-                h->stats.pipeline_adjoint = (adj3d_ws(h) && (h->nband == 0 || w.inj)) ? 1 : 0;
+            if (h->ndim == 3) {  // 0 one barrier per plane, 2 producer warp, 3 refill by the last compute warp
+                h->stats.pipeline_forward = !(h->opt_cluster3d & 1) ? h->opt_pipeline : 0;
+                h->stats.pipeline_adjoint = (adj3d_ws(h) && (h->nband == 0 || w.inj)) ? h->pipe_adj : 0;
             }
             h->stats.pipeline_rows = piped ? h->ws_rows : 0;
             h->stats.pipeline_rows_adjoint = piped ? h->ws_rows_adj : 0;

@@ -351,17 +351,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_step3d(const __grid_constant__ 
 constexpr int kWs3Threads = kThreads + 32;  // eight consumer warps + one producer warp
 
 // Pipelined variant (incident, nonlinear sampling, Born, and the adjoint without per-step Kahan
-// compensation): one producer warp streams the halo'd planes into the ring (per-slot full /
-// empty mbarriers, one arrival per consumer warp on release), so the consumer warps never meet
-// at a CTA-wide barrier inside the plane loop; each releases the oldest plane of its window as
-// soon as it is done with it.  The adjoint's receiver injection R^T r^n comes from the
+// compensation): the halo'd planes stream into the ring against per-slot full mbarriers, and the
+// compute warps never meet at a CTA-wide barrier inside the plane loop; each releases the oldest
+// plane of its window as soon as it is done with it.  With PROD, one producer warp waits on
+// per-slot empty mbarriers (one arrival per compute warp) and issues the refills; without it,
+// each compute warp counts itself out of the slot on a shared counter and the last of the eight
+// issues the slot's next TMA load itself, so no warp polls for free slots and the CTA is eight
+// warps, which leaves the compute warps more registers at three CTAs per SM.  The adjoint's receiver injection R^T r^n comes from the
 // segment's prebuilt band buffer (one float4 per thread on the planes that hold receivers)
 // instead of being assembled in shared memory.  The per-cell arithmetic is cells3, identical to
 // k_step3d.  Every wait is bounded.
-template <int MODE>
-__global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_constant__ StepParams3D p) {
+template <int MODE, bool PROD>
+__global__ void __launch_bounds__(PROD ? kWs3Threads : kThreads, 3) k_step3d_ws(const __grid_constant__ StepParams3D p) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[kRing], empty[kRing];
+    __shared__ uint32_t released[kRing];  // without PROD: compute-warp releases of each slot, cumulative
     // receiver CSR bounds of this column tile's planes (sampling), or each plane's injection
     // band, -1 without receivers (adjoint)
     __shared__ int srec[kZCMax3D + 1];
@@ -392,14 +396,21 @@ __global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_const
         for (int i = 0; i < kRing; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], kThreads / 32);
+            released[i] = 0u;
         }
         fence_mbar_init();
     }
     if (SAMPLE && tid <= nloc) srec[tid] = M.rec_ptr[(tyi * M.tiles_x + txi) * M.Nz + z0 + tid];
     if (ADJ && tid < nloc) srec[tid] = (M.rrow && M.inj) ? M.rrow[z0 + tid] : -1;
     __syncthreads();
+    if (!PROD && tid == 0) {  // the first kRing planes; the compute warps issue the rest
+        for (int k = 0; k < min(kRing, nplanes); ++k) {
+            mbar_expect_tx(&full[k], kPlaneBytes3);
+            tma_load_4d(smem + k * kPlane3, &M.tm, x0 - 4, y0 - 4, z0 - 4 + k, vol_cur, &full[k]);
+        }
+    }
 
-    if (warp == kThreads / 32) {  // ---------------- producer warp
+    if (PROD && warp == kThreads / 32) {  // ---------------- producer warp
         if (lane != 0) return;
         int sl = 0;
         uint32_t eph = 0;  // phase of empty[sl] to wait for, once the ring has wrapped
@@ -474,7 +485,20 @@ __global__ void __launch_bounds__(kWs3Threads, 3) k_step3d_ws(const __grid_const
         if (lane == 0) {  // this warp is done with plane k = iz (the bottom of its window)
             int sf = slot_c - 4;
             sf += (sf < 0) ? kRing : 0;
-            mbar_arrive(&empty[sf]);
+            if (PROD) {
+                mbar_arrive(&empty[sf]);
+            } else {
+                // the slot's use u = iz / kRing ends with the (8u + 8)-th release: that warp
+                // refills the slot with ring plane iz + kRing
+                const uint32_t old = atom_add_acqrel_shared(&released[sf], 1u);
+                const uint32_t last = (uint32_t)(kThreads / 32) * (uint32_t)(iz / kRing + 1) - 1u;
+                const int k = iz + kRing;
+                if (old == last && k < nplanes) {
+                    fence_proxy_async_shared();
+                    mbar_expect_tx(&full[sf], kPlaneBytes3);
+                    tma_load_4d(smem + sf * kPlane3, &M.tm, x0 - 4, y0 - 4, z0 - 4 + k, vol_cur, &full[sf]);
+                }
+            }
         }
         slot_c = (slot_c + 1 == kRing) ? 0 : slot_c + 1;
         if (++slot_w == kRing) {
@@ -962,13 +986,14 @@ cudaError_t launch_adj3d_cluster(int G, bool kahan, const StepParams3D& p, cudaS
     return cudaErrorInvalidValue;
 }
 
-template <int MODE>
+template <int MODE, bool PROD>
 static cudaError_t launch3_ws(const StepParams3D& p, dim3 grid, cudaStream_t st) {
     const size_t sm = (size_t)kRing * kPlaneBytes3;
     // set on every launch (a host-side attribute, no stream work): no shared state between threads
-    cudaError_t e = cudaFuncSetAttribute(k_step3d_ws<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_step3d_ws<MODE, PROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_step3d_ws<MODE><<<grid, kWs3Threads, sm, st>>>(p);
+    k_step3d_ws<MODE, PROD><<<grid, PROD ? kWs3Threads : kThreads, sm, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -981,20 +1006,32 @@ static cudaError_t launch3(const StepParams3D& p, dim3 grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_step3d(int mode, bool kahan, bool pipelined, const StepParams3D& p, cudaStream_t st) {
+template <bool PROD>
+static cudaError_t launch3_ws_mode(int mode, bool kahan, const StepParams3D& p, dim3 grid, cudaStream_t st,
+                                   bool* done) {
+    *done = true;
+    switch (mode) {
+        case STEP3_INC: return launch3_ws<STEP3_INC, PROD>(p, grid, st);
+        case STEP3_INC_SAMPLE: return launch3_ws<STEP3_INC_SAMPLE, PROD>(p, grid, st);
+        case STEP3_BORN: return launch3_ws<STEP3_BORN, PROD>(p, grid, st);
+        case STEP3_ADJ:  // the per-step Kahan adjoint keeps the one-barrier-per-plane kernel
+            if (!kahan) return launch3_ws<STEP3_ADJ, PROD>(p, grid, st);
+            break;
+        default: break;
+    }
+    *done = false;
+    return cudaSuccess;
+}
+
+cudaError_t launch_step3d(int mode, bool kahan, int pipeline, const StepParams3D& p, cudaStream_t st) {
     const ModelStep3D& M = p.m;
     dim3 grid(M.tiles_x * M.tiles_y * M.zchunks * M.nfield, M.nshots);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    if (pipelined) {
-        switch (mode) {
-            case STEP3_INC: return launch3_ws<STEP3_INC>(p, grid, st);
-            case STEP3_INC_SAMPLE: return launch3_ws<STEP3_INC_SAMPLE>(p, grid, st);
-            case STEP3_BORN: return launch3_ws<STEP3_BORN>(p, grid, st);
-            case STEP3_ADJ:  // the per-step Kahan adjoint keeps the one-barrier-per-plane kernel
-                if (!kahan) return launch3_ws<STEP3_ADJ>(p, grid, st);
-                break;
-            default: break;
-        }
+    if (pipeline) {  // 2: producer warp; 3: the last compute warp out of a slot refills it
+        bool done = false;
+        const cudaError_t e = (pipeline == 3) ? launch3_ws_mode<false>(mode, kahan, p, grid, st, &done)
+                                              : launch3_ws_mode<true>(mode, kahan, p, grid, st, &done);
+        if (done) return e;
     }
     switch (mode) {
         case STEP3_INC: return launch3<STEP3_INC, false>(p, grid, st);

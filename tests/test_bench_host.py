@@ -31,7 +31,8 @@ def test_kernel_labels_name_the_source_files():
     assert bench.kernel_label(0, True)[1] == "stencil2d.cu"
     assert bench.kernel_label(0, False, ndim=3)[1] == "stencil3d.cu"
     assert "k_adj3d_cl<G=4" in bench.kernel_label(0, True, ndim=3, cluster=True, group=4)[0]
-    assert bench.kernel_label(1, True, ndim=3)[0].startswith("k_step3d_ws<ADJ>")
+    assert bench.kernel_label(2, True, ndim=3)[0].startswith("k_step3d_ws<ADJ>")
+    assert bench.kernel_label(3, True, ndim=3)[0].startswith("k_step3d_ws[last-warp refill]<ADJ>")
     assert bench.kernel_label(0, True, ndim=3)[0].startswith("k_step3d<ADJ>")
     assert bench.kernel_label(3, False, time_block=2)[0].startswith("k_fwd2d_tb")
     assert bench.kernel_label(3, False, time_block=1)[0].startswith("k_fwd2d_ws")   # one level per launch
@@ -43,7 +44,8 @@ def test_kernel_labels_name_the_source_files():
 def test_committed_traffic_is_keyed_by_source_and_variant():
     with open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")) as f:
         e = json.load(f)["fwd_born"]
-    fresh = e["source_sha"] == bench.kernel_source_hash(e["source"])
+    fresh = e["source_sha"] == bench.kernel_source_hash(e["source"]) and all(
+        bench.kernel_source_hash(f) == h for f, h in e.get("deps", {}).items())
     got = bench.ncu_traffic("fwd_born", e["source"], dict(e["variant"]))
     assert got == (float(e["dram_bytes_per_launch"]) if fresh else None)
     other = {k: (v + 1 if isinstance(v, int) else v) for k, v in e["variant"].items()}

@@ -59,24 +59,26 @@ def test_born_data_3d(cuda_device, small3d):
 
 
 def test_forward_kernels_3d_agree(cuda_device, small3d):
-    """The producer-warp pipelined 3D kernels (forward, and the adjoint with its receiver injection
-    from the per-segment band buffer) and the one-barrier-per-plane kernels (injection assembled in
-    shared memory) run the same per-cell arithmetic: F and H agree bit for bit (no grid cell holds
-    more than two receivers here, so the injection sums cannot differ in order)."""
+    """The pipelined 3D kernels (forward, and the adjoint with its receiver injection from the
+    per-segment band buffer), with the ring refilled by a producer warp (2) or by the last compute
+    warp out of a slot (3), and the one-barrier-per-plane kernels (0; injection assembled in shared
+    memory) run the same per-cell arithmetic: F and H agree bit for bit (no grid cell holds more
+    than two receivers here, so the injection sums cannot differ in order)."""
     wl, prob, born, hes = small3d
     y = dev(wl.trials)
     out = []
-    for pipe in (0, 2):
+    for pipe in (0, 2, 3):
         p = make_probe(wl)
         p.set_option("pipeline", pipe)
         out.append((p.apply_F(y), p.apply_H(y)))
         st = p.stats()
-        assert st["pipeline_forward"] == (1 if pipe else 0)
-        assert st["pipeline_adjoint"] == (1 if pipe else 0)
-    assert torch.equal(out[0][0], out[1][0])
-    assert torch.equal(out[0][1], out[1][1])
+        assert st["pipeline_forward"] == pipe
+        assert st["pipeline_adjoint"] == pipe
+    for o in out[1:]:
+        assert torch.equal(out[0][0], o[0])
+        assert torch.equal(out[0][1], o[1])
     for b in range(2):
-        assert rel(out[1][1][b].cpu().numpy(), hes[b]) < 1e-4
+        assert rel(out[2][1][b].cpu().numpy(), hes[b]) < 1e-4
 
 
 def test_plane_chunks_3d_give_identical_bits(cuda_device, small3d):
