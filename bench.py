@@ -963,8 +963,10 @@ def main():
     adj_name, adj_src = kernel_label(stats["pipeline_adjoint"], True, len(wl.shape), bool(cl & 2),
                                      stats["shot_group"])
     if is3d:
-        fwd_var = {"shot_wave": stats["shot_wave"], "trials": ntr}
-        adj_var = {"shot_wave": stats["shot_wave"], "shot_group": stats["shot_group"], "trials": ntr}
+        fwd_var = {"shot_wave": stats["shot_wave"], "trials": ntr, "pipeline_forward": stats["pipeline_forward"],
+                   "planes_3d": stats["planes_3d"]}
+        adj_var = {"shot_wave": stats["shot_wave"], "shot_group": stats["shot_group"], "trials": ntr,
+                   "pipeline_adjoint": stats["pipeline_adjoint"], "planes_3d": stats["planes_3d"]}
         fwd_traffic = ncu_traffic("fwd3d", fwd_src, fwd_var)
         adj_traffic = ncu_traffic("adj3d", adj_src, adj_var)
     else:
