@@ -509,7 +509,13 @@ def experiment_trials(a):
     fam["white"] = (yw, H(yw))
     yt = torch.tensor(random_sign_trials(wl.m0, wl.h, 2199, p=1), device=dev)
     xt = H(yt)[0].contiguous()
+    # a second test trial inside the range of H (y_r = H z / ||H z||): it has no component that H
+    # annihilates, which no preconditioner can recover (the role of the paper's illumination mask)
+    yr = xt[None].clone()
+    yr /= torch.linalg.vector_norm(yr)
+    xr = H(yr)[0].contiguous()
     Ps, mse, fit_ms, rank_deficient = [], {k: [] for k in fam}, [], []
+    mse_r = {k: [] for k in fam}
     for sp, ang, nrad in _trial_bases():
         b = Basis(2, sp, ang, nrad, L, -1.0, 16)
         Ps.append(b.P)
@@ -519,20 +525,26 @@ def experiment_trials(a):
                 (c, _), dt = _sync_time(torch, lambda: p.fit(b, yy, xx))
             except ProbeError as ex:  # columns numerically rank deficient for this family and basis
                 mse[k].append(None)
+                mse_r[k].append(None)
                 rank_deficient.append([k, b.P, str(ex)[:80]])
                 continue
             tf += dt
             pre = p.apply_precond(b, c, xt)
             mse[k].append(float(torch.linalg.vector_norm((pre - yt[0]).double()) /
                                 torch.linalg.vector_norm(yt[0].double())))
+            pre_r = p.apply_precond(b, c, xr)
+            mse_r[k].append(float(torch.linalg.vector_norm((pre_r - yr[0]).double()) /
+                                  torch.linalg.vector_norm(yr[0].double())))
         fit_ms.append(tf / len(fam) * 1e3)
     print(json.dumps({
         "experiment": "trial_functions", "workload": "2d-501x501-nt2500-32shots", "trials_per_family": npf,
-        "P": Ps, "generalisation_mse": mse, "fit_ms_mean": fit_ms, "rank_deficient": rank_deficient,
+        "P": Ps, "generalisation_mse": mse, "generalisation_mse_range": mse_r, "fit_ms_mean": fit_ms,
+        "rank_deficient": rank_deficient,
         "h_applies": n_h, "ms_per_h_apply": t_h / max(n_h, 1) * 1e3, "krylov_ms": tk * 1e3,
         "how": "fit of sum_i c_i B_i ~ H^{-1} on (y_j, H y_j) of each family (CholeskyQR2, FP64), then "
                "||y_t - M(H y_t)|| / ||y_t|| on an independent random-sign trial y_t; Kn from F*d of the "
-               "configuration's 200-bump perturbation; white: y = H n, n iid N(0,1)"}))
+               "configuration's 200-bump perturbation; white: y = H n, n iid N(0,1); _range: the same error on "
+               "y_r = H y_t / ||H y_t||, a test trial inside the range of H"}))
 
 
 def experiment_eps_rank(a):
@@ -998,7 +1010,7 @@ def main():
                    "tile_z": stats["tile_z"], "pipeline_forward": stats["pipeline_forward"],
                    "pipeline_adjoint": stats["pipeline_adjoint"], "time_block": stats["time_block"],
                    "cuda_graph": not is3d,
-                   "autotuned": (not a.fixed) and not is3d,
+                   "autotuned": not a.fixed,
                    "l2": (f"inputs larger than L2: {wl.ns} shots x {2 + 2 * ntr} field planes x "
                           f"{wl.cells_padded() * 4 / 1e6:.2f} MB = {live_mb:.0f} MB live state per step "
                           f"> {L2_BYTES / 1e6:.0f} MB L2; no flush") if live_mb * 1e6 > L2_BYTES else
