@@ -941,8 +941,12 @@ probe_status autotune_3d(const Job& jb, FwdKind kind, bool adjoint, cudaStream_t
         pa.m.seg_first = 1;
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    CK(h, cudaEventCreate(&e0));
-    CK(h, cudaEventCreate(&e1));
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(h, ce, "autotuner events");
+    }
     // times `body` (which launches on st) and keeps the minimum in *best
     auto timed = [&](float* best, auto body) -> probe_status {
         cudaEventRecord(e0, st);
