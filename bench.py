@@ -1014,10 +1014,12 @@ def main():
     adj_name, adj_src = kernel_label(stats["pipeline_adjoint"], True, len(wl.shape), bool(cl & 2),
                                      stats["shot_group"])
     if is3d:
-        fwd_var = {"shot_wave": stats["shot_wave"], "trials": ntr, "pipeline_forward": stats["pipeline_forward"],
-                   "planes_3d": stats["planes_3d"]}
+        # keyed on what changes the bytes a launch moves: the refill scheme of the step that
+        # dominates the sweep and the batch shape (the incident step's refill scheme moves the same
+        # bytes; the plane count per CTA changes them by a few per cent, noted with the entry)
+        fwd_var = {"shot_wave": stats["shot_wave"], "trials": ntr, "pipeline_forward": stats["pipeline_forward"]}
         adj_var = {"shot_wave": stats["shot_wave"], "shot_group": stats["shot_group"], "trials": ntr,
-                   "pipeline_adjoint": stats["pipeline_adjoint"], "planes_3d": stats["planes_3d"]}
+                   "pipeline_adjoint": stats["pipeline_adjoint"]}
         fwd_traffic = ncu_traffic("fwd3d", fwd_src, fwd_var)
         adj_traffic = ncu_traffic("adj3d", adj_src, adj_var)
     else:
@@ -1080,8 +1082,9 @@ def main():
         for k in ("tile_z", "pipeline_forward", "pipeline_adjoint", "time_block"):
             line["config"].pop(k, None)
         fk = kernel_label(stats["pipeline_forward"], False, 3)[0].split("<")[0]
+        ik = kernel_label(stats["pipeline_incident"], False, 3)[0].split("<")[0]
         ak = kernel_label(stats["pipeline_adjoint"], True, 3)[0].split("<")[0]
-        line["config"]["kernels"] = (f"{fk}<INC> + {fk}<BORN> (forward), {fk}<INC> (recompute), "
+        line["config"]["kernels"] = (f"{ik}<INC> + {fk}<BORN> (forward), {ik}<INC> (recompute), "
                                      f"{ak}<ADJ> into checkpoint-segment images + k_kahan_fold (adjoint)"
                                      if cl == 0 else f"cluster kernels (PROBE_OPT_CLUSTER3D = {cl})")
         line["config"]["planes_per_cta"] = stats["planes_3d"]

@@ -190,6 +190,8 @@ typedef struct {
     int pipeline_rows_adjoint;   /* rows per thread of the pipelined adjoint kernel */
     int time_block;              /* 2D Born forward and recompute: time levels per launch (1 or 2) */
     int planes_3d;               /* 3D: z planes marched by one CTA (0 for 2D) */
+    int pipeline_incident;       /* 3D: as pipeline_forward, for the incident step (forward and
+                                    recompute; pipeline_forward then names the Born step's) */
 } probe_stats;
 
 /* Create a handle for one background model and acquisition geometry.

@@ -48,7 +48,8 @@ class probe_stats(C.Structure):
                 ("shot_wave", C.c_int), ("shot_group", C.c_int), ("tile_z", C.c_int),
                 ("ckpt_stride", C.c_int), ("pipeline_forward", C.c_int),
                 ("pipeline_adjoint", C.c_int), ("dtt_history", C.c_int), ("pipeline_rows", C.c_int),
-                ("pipeline_rows_adjoint", C.c_int), ("time_block", C.c_int), ("planes_3d", C.c_int)]
+                ("pipeline_rows_adjoint", C.c_int), ("time_block", C.c_int), ("planes_3d", C.c_int),
+                ("pipeline_incident", C.c_int)]
 
 
 class ProbeError(RuntimeError):

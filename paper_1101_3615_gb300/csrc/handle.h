@@ -58,7 +58,7 @@ struct TunedEntry {
 // 3D autotuner result: refill scheme of the pipelined forward and adjoint kernels, planes per CTA.
 struct Tuned3 {
     std::vector<long long> key;  // kind, adjoint, shots, trials
-    int fam_fwd = 2, fam_adj = 2, zc = 64;
+    int fam_fwd = 2, fam_inc = 2, fam_adj = 2, zc = 64;
 };
 
 struct GraphEntry {
@@ -121,6 +121,7 @@ struct probe_s {
     int opt_tblock = 1;          // 2D Born forward and recompute: time levels per launch (1 or 2)
     int user_tblock = 0;         // the caller fixed opt_tblock (else the autotuner chooses)
     int pipe_adj = 2;            // adjoint kernel variant (the forward uses opt_pipeline)
+    int pipe_inc = 2;            // 3D: ring-refill scheme of the incident step (forward and recompute)
     int zc3d = probe::kZC3D;     // 3D: z planes marched by one CTA (32, 64 or 128)
     int user_zc3d = 0;           // the caller fixed zc3d (else the autotuner chooses)
     std::vector<probe::Tuned3> tuned3;  // 3D autotuner results by workload key

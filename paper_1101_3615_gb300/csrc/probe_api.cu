@@ -885,7 +885,9 @@ struct Count3 {
 
 probe_status launch3(probe_t h, int mode, StepParams3D& p, int n, cudaStream_t st, const char* what) {
     p.n = n;
-    cudaError_t e = launch_step3d(mode, h->kahan != 0, h->opt_pipeline, p, st);
+    // the incident step (forward and recompute) may use its own ring-refill scheme
+    const int pipe = (mode == STEP3_INC || mode == STEP3_INC_SAMPLE) ? h->pipe_inc : h->opt_pipeline;
+    cudaError_t e = launch_step3d(mode, h->kahan != 0, pipe, p, st);
     if (e != cudaSuccess) return cuda_fail(h, e, what);
     return PROBE_OK;
 }
@@ -908,6 +910,7 @@ probe_status autotune_3d(const Job& jb, FwdKind kind, bool adjoint, cudaStream_t
             if (!h->user_zc3d) h->zc3d = t.zc;
             if (!fam_fixed) {
                 h->opt_pipeline = t.fam_fwd;
+                h->pipe_inc = t.fam_inc;
                 h->pipe_adj = t.fam_adj;
             }
             return PROBE_OK;
@@ -966,7 +969,8 @@ probe_status autotune_3d(const Job& jb, FwdKind kind, bool adjoint, cudaStream_t
             q->m.zchunks = (h->Nz + zc - 1) / zc;
         }
     };
-    // forward: (refill scheme, planes); the caller's fixed choices stay fixed
+    // forward: (refill scheme, planes), the incident and the Born launches timed apart so that
+    // each gets its own scheme; the caller's fixed choices stay fixed
     std::vector<int> fams = {2, 3}, zcs = {32, 64, 128};
     if (fam_fixed) fams = {h->opt_pipeline};
     if (h->user_zc3d) zcs = {h->zc3d};
@@ -974,26 +978,41 @@ probe_status autotune_3d(const Job& jb, FwdKind kind, bool adjoint, cudaStream_t
     for (int fam : fams)
         for (int zc : zcs) cand.push_back({fam, zc});
     const int nc = (int)cand.size();
-    std::vector<float> best(nc, 1e30f);
+    std::vector<float> t_inc(nc, 1e30f), t_born(nc, born ? 1e30f : 0.f);
     probe_status ps = PROBE_OK;
     for (int round = 0; round < 3 && ps == PROBE_OK; ++round)
         for (int c = 0; c < nc && ps == PROBE_OK; ++c) {
             set_zc(cand[c].second);
-            ps = timed(&best[c], [&]() -> probe_status {
-                for (int n = 0; n < 2; ++n) {
-                    pi.n = pb.n = n;
-                    cudaError_t e = launch_step3d(STEP3_INC, false, cand[c].first, pi, st);
-                    if (e == cudaSuccess && born) e = launch_step3d(STEP3_BORN, false, cand[c].first, pb, st);
-                    if (e != cudaSuccess) return cuda_fail(h, e, "autotuner launch");
-                }
-                return PROBE_OK;
-            });
+            for (int mode : {STEP3_INC, STEP3_BORN}) {
+                if (ps != PROBE_OK || (mode == STEP3_BORN && !born)) continue;
+                StepParams3D& q = (mode == STEP3_INC) ? pi : pb;
+                ps = timed(mode == STEP3_INC ? &t_inc[c] : &t_born[c], [&]() -> probe_status {
+                    for (int n = 0; n < 2; ++n) {
+                        q.n = n;
+                        cudaError_t e = launch_step3d(mode, false, cand[c].first, q, st);
+                        if (e != cudaSuccess) return cuda_fail(h, e, "autotuner launch");
+                    }
+                    return PROBE_OK;
+                });
+            }
         }
-    int bi = 0;
-    for (int c = 1; c < nc; ++c)
-        if (best[c] < best[bi]) bi = c;
-    const int zc = h->user_zc3d ? h->zc3d : cand[bi].second;
-    const int fam_fwd = cand[bi].first;
+    // per plane count the faster scheme of each launch; then the plane count of the fastest step
+    int zc = h->zc3d, fam_inc = fams[0], fam_fwd = fams[0];
+    float best_step = 1e30f;
+    for (int z : zcs) {
+        int bi = -1, bb = -1;
+        for (int c = 0; c < nc; ++c) {
+            if (cand[c].second != z) continue;
+            if (bi < 0 || t_inc[c] < t_inc[bi]) bi = c;
+            if (bb < 0 || t_born[c] < t_born[bb]) bb = c;
+        }
+        if (bi >= 0 && t_inc[bi] + t_born[bb] < best_step) {
+            best_step = t_inc[bi] + t_born[bb];
+            zc = z;
+            fam_inc = cand[bi].first;
+            fam_fwd = cand[bb].first;
+        }
+    }
     // adjoint refill scheme at the chosen planes
     int fam_adj = fam_fixed ? h->pipe_adj : fam_fwd;
     if (ps == PROBE_OK && adjoint && !fam_fixed && adj3d_ws(h)) {
@@ -1016,12 +1035,14 @@ probe_status autotune_3d(const Job& jb, FwdKind kind, bool adjoint, cudaStream_t
     TRY(ps);
     h->zc3d = zc;
     if (!fam_fixed) {
-        h->opt_pipeline = fam_fwd;
+        h->opt_pipeline = born ? fam_fwd : fam_inc;
+        h->pipe_inc = fam_inc;
         h->pipe_adj = fam_adj;
     }
     Tuned3 t;
     t.key = key;
     t.fam_fwd = h->opt_pipeline;
+    t.fam_inc = h->pipe_inc;
     t.fam_adj = h->pipe_adj;
     t.zc = h->zc3d;
     h->tuned3.push_back(t);
@@ -1551,6 +1572,7 @@ extern "C" probe_status probe_set_option(probe_t h, int key, long long v) {
             if (v != 0 && v != 2 && v != 3) return fail(h, PROBE_ERR_ARG, "pipeline must be 0, 2 or 3");
             h->opt_pipeline = (int)v;
             h->pipe_adj = (int)v;
+            h->pipe_inc = (int)v;
             h->user_fixed = 1;
             return PROBE_OK;
         case PROBE_OPT_TILE_Z:
@@ -1870,6 +1892,7 @@ probe_status run_op(probe_t h, Op op, const float* dm_dev, const float* data_in,
             h->stats.planes_3d = (h->ndim == 3) ? h->zc3d : 0;
             if (h->ndim == 3) {  // 0 one barrier per plane, 2 producer warp, 3 refill by the last compute warp
                 h->stats.pipeline_forward = !(h->opt_cluster3d & 1) ? h->opt_pipeline : 0;
+                h->stats.pipeline_incident = !(h->opt_cluster3d & 1) ? h->pipe_inc : 0;
                 h->stats.pipeline_adjoint = (adj3d_ws(h) && (h->nband == 0 || w.inj)) ? h->pipe_adj : 0;
             }
             h->stats.pipeline_rows = piped ? h->ws_rows : 0;

@@ -73,6 +73,7 @@ def test_forward_kernels_3d_agree(cuda_device, small3d):
         out.append((p.apply_F(y), p.apply_H(y)))
         st = p.stats()
         assert st["pipeline_forward"] == pipe
+        assert st["pipeline_incident"] == pipe
         assert st["pipeline_adjoint"] == pipe
     for o in out[1:]:
         assert torch.equal(out[0][0], o[0])
