@@ -66,6 +66,8 @@ def parse():
                          "precond or CPU legs): the command whose kernel launches an ncu launch list records")
     ap.add_argument("--tblock", type=int, default=0, help="2D: time levels per launch (1 or 2; 0: autotuned)")
     ap.add_argument("--planes3d", type=int, default=0, help="3D: z planes per CTA (32, 64, 128; 0: autotuned)")
+    ap.add_argument("--overlap3d", type=int, default=-1,
+                    help="3D Born forward: 1 incident step n+1 beside Born step n on two streams, 0 one stream")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-history", action="store_true",
                     help="skip the extra measurement with the full Dtt history resident")
@@ -126,6 +128,8 @@ def profile_run(a, wl):
         p.set_option("tblock", a.tblock)
     if a.planes3d and len(wl.shape) == 3:
         p.set_option("planes3d", a.planes3d)
+    if a.overlap3d >= 0 and len(wl.shape) == 3:
+        p.set_option("overlap3d", a.overlap3d)
     dm = torch.tensor(wl.trials, device=dev)
     if a.profile == "fwd":
         run = lambda: p.apply_F(dm)
@@ -800,6 +804,8 @@ def main():
         p.set_option("tblock", a.tblock)
     if a.planes3d and is3d:
         p.set_option("planes3d", a.planes3d)
+    if a.overlap3d >= 0 and is3d:
+        p.set_option("overlap3d", a.overlap3d)
     dm = torch.tensor(wl.trials, device=dev)
     out = torch.empty_like(dm)
     stream = torch.cuda.current_stream(dev)

@@ -143,6 +143,11 @@ typedef enum {
                                     halo and recomputes the first level on the tile plus 4 cells, which
                                     halves the state traffic per level); 0 (default) = chosen by the
                                     autotuner.  Both give the same bits. */
+    PROBE_OPT_OVERLAP3D = 16,    /* 3D Born forward: 1 (default) = the incident step n+1 runs on a second
+                                    stream concurrently with the Born step n (the Dtt plane of the
+                                    incident step is double-buffered), so each launch's last, partly
+                                    filled wave of CTAs overlaps the other's; 0 = one stream.  Same
+                                    bits either way. */
     PROBE_OPT_PLANES3D = 15,     /* 3D: z planes one CTA marches through (32, 64 or 128; each CTA loads
                                     8 halo planes besides them); 0 (default) = chosen by the autotuner,
                                     which times the forward step kernels on the real workspace at each

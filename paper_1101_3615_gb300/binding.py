@@ -23,7 +23,7 @@ SNAP = {"fp32": 0, "bf16": 1, "fp16": 2}
 SOLVE = {"gd": 0, "cg": 1}
 OPT = {"check_finite": 1, "shot_wave": 2, "shot_group": 3, "use_graph": 4, "timing": 5, "tile_z": 6,
        "pipeline": 7, "dtt_history": 8, "autotune": 9, "pipe_rows": 10, "pipeline_adj": 11, "pipe_rows_adj": 12,
-       "cluster3d": 13, "tblock": 14, "planes3d": 15}
+       "cluster3d": 13, "tblock": 14, "planes3d": 15, "overlap3d": 16}
 
 
 class probe_grid(C.Structure):

@@ -122,6 +122,7 @@ struct probe_s {
     int user_tblock = 0;         // the caller fixed opt_tblock (else the autotuner chooses)
     int pipe_adj = 2;            // adjoint kernel variant (the forward uses opt_pipeline)
     int pipe_inc = 2;            // 3D: ring-refill scheme of the incident step (forward and recompute)
+    int opt_overlap3d = 1;       // 3D Born forward: incident step n+1 concurrent with Born step n
     int zc3d = probe::kZC3D;     // 3D: z planes marched by one CTA (32, 64 or 128)
     int user_zc3d = 0;           // the caller fixed zc3d (else the autotuner chooses)
     std::vector<probe::Tuned3> tuned3;  // 3D autotuner results by workload key
@@ -140,6 +141,10 @@ struct probe_s {
     // captured sweeps (PROBE_OPT_USE_GRAPH), replayed on gstream
     cudaStream_t gstream = nullptr;
     cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+    // 3D forward with the incident step n+1 overlapping the Born step n: the Born steps run on
+    // ostream; ov_inc[s] / ov_born[s] mark the incident / Born step that last used Dtt slot s
+    cudaStream_t ostream = nullptr;
+    cudaEvent_t ov_inc[2] = {nullptr, nullptr}, ov_born[2] = {nullptr, nullptr};
     std::vector<probe::GraphEntry> graphs;
     long long graph_generation = -1;
 };

@@ -183,6 +183,8 @@ void ws_bytes(probe_t h, int nb, int with_ckpt, int with_data, double* per_shot,
         ps += (double)(h->nt - 1) * F4;
     else if (with_ckpt)
         ps += (double)h->nck * ckpt_bytes_per_shot(h->snap, h->F) + (double)h->K * F4 + 16.0 * h->nck;
+    else if (h->ndim == 3)
+        ps += 2.0 * F4;  // Dtt u^n of two steps (Born source)
     if (with_data) ps += (double)nb * h->nt * h->nr * 4.0;
     if (h->ndim == 3 && with_ckpt) {
         ps += 2.0 * nb * F4;  // per-shot images + compensation
@@ -271,7 +273,7 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
         TRY(alloc((void**)&w.absmax, (size_t)W * 2 * 4));
         TRY(alloc((void**)&w.dtt, (size_t)W * h->K * F * 4));
     } else if (h->ndim == 3) {
-        TRY(alloc((void**)&w.dtt, (size_t)W * F * 4));  // Dtt u^n of the current step (Born source)
+        TRY(alloc((void**)&w.dtt, (size_t)W * 2 * F * 4));  // Dtt u^n of two steps (Born source)
     }
     TRY(alloc((void**)&w.img, (size_t)G * std::max(nb, 1) * F * 4));
     TRY(alloc((void**)&w.comp, (size_t)G * std::max(nb, 1) * F * 4));
@@ -287,7 +289,7 @@ probe_status ensure_ws(probe_t h, int W, int nb, int with_ckpt, int with_data) {
     CK(h, cudaMemset(w.u, 0, (size_t)W * 2 * F * 4));
     CK(h, cudaMemset(w.f, 0, (size_t)W * std::max(nb, 1) * 2 * F * 4));
     w.history = history;
-    w.dtt_slots = history ? h->nt - 1 : (with_ckpt ? h->K : 1);
+    w.dtt_slots = history ? h->nt - 1 : (with_ckpt ? h->K : (h->ndim == 3 ? 2 : 1));
     if (w.dtt) CK(h, cudaMemset(w.dtt, 0, (size_t)W * w.dtt_slots * F * 4));
     w.W = W;
     w.nb = nb;
@@ -827,7 +829,7 @@ probe_status run_adjoint(Sweep& sw) {
 // ---------------------------------------------------------------------------
 // 3D sweeps: one launch per field kind and step (incident, Born trials, adjoint).
 // ---------------------------------------------------------------------------
-long long dtt_stride3(probe_t h) { return (long long)(h->ws.with_ckpt ? h->K : 1) * h->F; }
+long long dtt_stride3(probe_t h) { return (long long)(h->ws.with_ckpt ? h->K : 2) * h->F; }
 
 void fill3d(const Job& jb, ModelStep3D& m) {
     probe_t h = jb.h;
@@ -1049,6 +1051,16 @@ probe_status autotune_3d(const Job& jb, FwdKind kind, bool adjoint, cudaStream_t
     return PROBE_OK;
 }
 
+probe_status ensure_overlap_stream(probe_t h) {
+    if (h->ostream) return PROBE_OK;
+    CK(h, cudaStreamCreateWithFlags(&h->ostream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+        CK(h, cudaEventCreateWithFlags(&h->ov_inc[i], cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->ov_born[i], cudaEventDisableTiming));
+    }
+    return PROBE_OK;
+}
+
 probe_status run_forward3d(const Job& jb, FwdKind kind, bool ckpt, cudaStream_t st, Count3& c) {
     probe_t h = jb.h;
     Workspace& w = h->ws;
@@ -1088,6 +1100,17 @@ probe_status run_forward3d(const Job& jb, FwdKind kind, bool ckpt, cudaStream_t 
         pf.m2 = pb.m;
         pf.m2.Din = nullptr;
     }
+    // overlapped forward: the incident step n writes Dtt u^n into slot n & 1 on `st`; the Born
+    // step n reads it on the second stream after the incident step's event, and the incident step
+    // n + 2 (the slot's next writer) waits for the Born step n's event.  Both streams are joined
+    // to `st` before the sampling.
+    const bool overlap = born && !fused && h->opt_overlap3d && w.dtt_slots >= 2;
+    if (overlap) TRY(ensure_overlap_stream(h));
+    cudaStream_t sb = overlap ? h->ostream : st;
+    if (overlap) {  // the Born stream starts after everything queued on st so far
+        CK(h, cudaEventRecord(h->ov_inc[0], st));
+        CK(h, cudaStreamWaitEvent(sb, h->ov_inc[0], 0));
+    }
     for (int n = 0; n < h->nt - 1; ++n) {
         if (ckpt && n % h->K == 0) {
             const int k = n / h->K;
@@ -1105,12 +1128,25 @@ probe_status run_forward3d(const Job& jb, FwdKind kind, bool ckpt, cudaStream_t 
             c.fwd++;
             continue;
         }
+        const int slot = overlap ? (n & 1) : 0;
+        if (overlap && n >= 2) CK(h, cudaStreamWaitEvent(st, h->ov_born[slot], 0));
+        if (born) pi.m.Dout = w.dtt + (long long)slot * h->F;
         TRY(launch3(h, imode, pi, n, st, "incident step launch"));
         c.fwd++;
         if (born) {
-            TRY(launch3(h, STEP3_BORN, pb, n, st, "Born step launch"));
+            if (overlap) {
+                CK(h, cudaEventRecord(h->ov_inc[slot], st));
+                CK(h, cudaStreamWaitEvent(sb, h->ov_inc[slot], 0));
+            }
+            pb.m.Din = w.dtt + (long long)slot * h->F;
+            TRY(launch3(h, STEP3_BORN, pb, n, sb, "Born step launch"));
+            if (overlap) CK(h, cudaEventRecord(h->ov_born[slot], sb));
             c.fwd++;
         }
+    }
+    if (overlap) {  // join the Born stream back into st
+        CK(h, cudaEventRecord(h->ov_born[0], sb));
+        CK(h, cudaStreamWaitEvent(st, h->ov_born[0], 0));
     }
     if (born || kind == FWD_INCIDENT_SAMPLE) {
         cudaError_t e = launch_sample(born ? w.f : w.u, (long long)(born ? jb.nb : 1) * 2 * h->F, 2 * h->F,
@@ -1488,6 +1524,11 @@ extern "C" void probe_destroy(probe_t h) {
     if (h->gstream) cudaStreamDestroy(h->gstream);
     if (h->gev_in) cudaEventDestroy(h->gev_in);
     if (h->gev_out) cudaEventDestroy(h->gev_out);
+    if (h->ostream) cudaStreamDestroy(h->ostream);
+    for (int i = 0; i < 2; ++i) {
+        if (h->ov_inc[i]) cudaEventDestroy(h->ov_inc[i]);
+        if (h->ov_born[i]) cudaEventDestroy(h->ov_born[i]);
+    }
     fit_cache_destroy(h);
     free_ws(h->ws);
     void* ptrs[] = {h->d_m0, h->d_s0, h->d_wavelet, h->d_src, h->d_rec, h->d_rec_tile_ptr, h->d_rec_tile_idx,
@@ -1548,6 +1589,9 @@ extern "C" probe_status probe_set_option(probe_t h, int key, long long v) {
             if (v < 0 || v > 2) return fail(h, PROBE_ERR_ARG, "tblock must be 0, 1 or 2");
             h->user_tblock = v > 0 ? 1 : 0;
             h->opt_tblock = v > 0 ? (int)v : 1;
+            return PROBE_OK;
+        case PROBE_OPT_OVERLAP3D:
+            h->opt_overlap3d = v ? 1 : 0;
             return PROBE_OK;
         case PROBE_OPT_PLANES3D:
             if (v != 0 && v != 32 && v != 64 && v != 128)

@@ -82,6 +82,21 @@ def test_forward_kernels_3d_agree(cuda_device, small3d):
         assert rel(out[2][1][b].cpu().numpy(), hes[b]) < 1e-4
 
 
+def test_overlapped_forward_3d_gives_identical_bits(cuda_device, small3d):
+    """The Born forward with the incident step n+1 on a second stream beside the Born step n (the
+    incident step's Dtt plane double-buffered, events ordering each slot's writer after its last
+    reader) gives the same bits as the one-stream forward, for F and for H."""
+    wl, prob, born, hes = small3d
+    y = dev(wl.trials)
+    out = []
+    for ov in (0, 1):
+        p = make_probe(wl)
+        p.set_option("overlap3d", ov)
+        out.append((p.apply_F(y), p.apply_H(y)))
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+
+
 def test_plane_chunks_3d_give_identical_bits(cuda_device, small3d):
     """The z planes one CTA marches (32, 64, 128, or the autotuner's pick) only change how the
     grid is cut into CTAs: F and H are the same bits for every choice (34 padded planes here, so
